@@ -1,0 +1,341 @@
+"""Benchmark of the finite-difference acoustic path on GB300.
+
+One benchmark step = one full forward modelling run of the headline workload
+(512^3 physical + 40-cell layer = 592^3 points, SO 8, 1000 leapfrog steps,
+source injection and 512 receivers) through the C ABI.  Metric: Gpts/s =
+592^3 * 1000 / (device time of one step), whole-job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
+the workload (the path has no exchange step on one shot; replicas only), so
+scaling is weak and value = sum over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a few time steps of the full grid).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES_PER_POINT = 16  # read u^n, u^{n-1}, A; write u^{n+1}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("fd_step.cuh", "fd_step_inst.cuh", "fd_internal.h"):
+        with open(os.path.join(ROOT, "paper_2312_13094_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(w, seconds=15.0, max_steps=20):
+    """Gpts/s of the FP64 oracle (as it stands) on the full grid of the
+    workload for a few time steps; returns (rate, steps, cores, seconds)."""
+    import oracle
+    og = oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=w["space_order"] // 2, nbl=w["nbl"])
+    m = 1.0 / w["v"].astype(np.float64) ** 2
+    npts = int(np.prod(og.padded_shape))
+    steps, elapsed = 0, 0.0
+    state = None
+    # first a single step to size the sample, then as many as fit the budget
+    plan = [1]
+    while plan:
+        k = plan.pop()
+        t0 = time.perf_counter()
+        out = oracle.forward(og, m, k, w["src"], w["wavelet"], w["rec"],
+                             state=state, n0=steps)
+        dt = time.perf_counter() - t0
+        state = (out["u_prev"], out["u_cur"])
+        steps += k
+        elapsed += dt
+        if len(plan) == 0 and steps == 1:
+            more = int(max(0.0, seconds - dt) / max(dt, 1e-9))
+            more = min(more, max_steps - 1)
+            if more > 0:
+                plan.append(more)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return npts * steps / elapsed / 1e9, steps, cores, elapsed
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return
+    rates = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state worth timing
+    per = []
+    for _ in range(args.steps):
+        r, k, cores, el = cpu_oracle_rate(w, seconds=args.ref_seconds, max_steps=3)
+        rates.append(r)
+        per.append(el / k * w["nt"] * 1e3)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": "Gpts/s", "value": value, "unit": "Gpts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(per), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w),
+        "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{k} of {w['nt']} time steps of the full "
+                                   f"{'x'.join(map(str, _padded(w)))} grid per bench step; "
+                                   "ms_per_step extrapolated to the full run"},
+        "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _padded(w):
+    return [d + 2 * w["nbl"] for d in w["n"]]
+
+
+def _config(w):
+    return {"workload": w["name"], "grid_padded": _padded(w), "space_order": w["space_order"],
+            "nt": w["nt"], "nbl": w["nbl"], "receivers": len(w["rec"]),
+            "l2": "inputs larger than L2 (each field 0.85 GB vs 129 MB L2); no flush",
+            "parallelism": "replicas"}
+
+
+def run_ours(args, w, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2312_13094_gb300 import binding as fd
+
+    stream = torch.cuda.Stream()
+    npts = int(np.prod(_padded(w)))
+    nt = w["nt"]
+    nrec = len(w["rec"])
+    with torch.cuda.stream(stream):
+        g = fd.Grid.from_workload(w, device=local, stream=stream.cuda_stream)
+        v_dev = torch.from_numpy(w["v"]).cuda()
+        wav_dev = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+        rec_dev = torch.zeros((nt, nrec), device="cuda")
+        g.set_model(v_dev)
+
+        def one():
+            fd.check(g.forward(w["src"], wav_dev, w["rec"], rec_dev), "fd_forward")
+
+        for _ in range(args.warmup):
+            one()
+        torch.cuda.synchronize()
+        g.set_profiling(True)
+        launches0 = fd.fd_launch_count()
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop()
+        launches = fd.fd_launch_count() - launches0
+        ms = ev0.elapsed_time(ev1)
+        info = g.info()
+        g.set_profiling(False)
+
+        # end to end through the public API with host buffers (pinned)
+        e2e = None
+        if not args.no_e2e:
+            v_host = torch.from_numpy(w["v"]).pin_memory()
+            wav_host = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).pin_memory()
+            rec_host = torch.zeros((nt, nrec)).pin_memory()
+            for _ in range(1):
+                g.set_model(v_host)
+                fd.check(g.forward(w["src"], wav_host, w["rec"], rec_host), "fd_forward")
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.set_model(v_host)
+                fd.check(g.forward(w["src"], wav_host, w["rec"], rec_host), "fd_forward")
+                float(rec_host[-1, 0])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms = e0.elapsed_time(e1)
+            e2e = {"ms": e2e_ms,
+                   "h2d": v_host.numel() * 4 + wav_host.numel() * 4,
+                   "d2h": rec_host.numel() * 4}
+        g.close()
+
+    t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * npts * nt * args.steps / (ms_max * 1e-3) / 1e9
+    avg_launch_ms = info["step_ms"] / max(1, info["steps_timed"])
+    peak, peak_kind = _peaks()
+    achieved = ALGO_BYTES_PER_POINT * npts / (avg_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "Gpts/s", "value": value, "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(w),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": _traffic(w["name"]),
+                     "kernel": "fd::step_kernel (avg over the timed launches)",
+                     "algorithmic_bytes_per_launch": ALGO_BYTES_PER_POINT * npts,
+                     "avg_launch_ms": avg_launch_ms},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "tile": [info["tile_x"], info["tile_y"], info["zsplit"]],
+        "interior_gpts": world * int(np.prod(w["n"])) * nt * args.steps /
+        (ms_max * 1e-3) / 1e9,
+        "paper_context": {"value": 31.2, "unit": "Gpts/s",
+                          "what": "SO 8 acoustic, 1x A100-80, 1158^3 + ABC, 290 steps"},
+    }
+    if e2e:
+        line["e2e"] = {"value": world * npts * nt * args.steps / (e2e_max * 1e-3) / 1e9,
+                       "unit": "Gpts/s", "h2d_bytes_per_step": e2e["h2d"],
+                       "d2h_bytes_per_step": e2e["d2h"]}
+    if not args.no_cpu_baseline and world == 1:
+        r, k, cores, el = cpu_oracle_rate(w, seconds=args.ref_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{k} time steps of the full "
+                                          f"{'x'.join(map(str, _padded(w)))} grid "
+                                          f"({el:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="physical grid edge")
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    from paper_2312_13094_gb300 import workloads as wl
+    w = wl.acoustic_512(n=args.n, nt=args.nt)
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+    else:
+        run_ours(args, w, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * fd.h -- C ABI of libfd.so: explicit high-order finite-difference time
+ * stepping of the isotropic acoustic wave equation on one GB300 (sm_103a).
+ *
+ * The operation (paper: "Automated MPI-X code generation for scalable
+ * finite-difference solvers", Eq. 1 in App. A and Sec. IV-B/IV-C):
+ *
+ *     m(x) u_tt - Laplace(u) + eta(x) u_t = delta(x - x_s) q(t),
+ *     u = u_t = 0 at t = 0,   d(t) = u(t, x_r),   m = 1/c^2,
+ *
+ * discretised with the centred order-2R second-derivative stencil in each
+ * axis (space order SO = 2R, 2..16) and second-order leapfrog in time, with a
+ * sponge layer of `nbl` cells added outside each face of the physical grid in
+ * which eta = m * gamma(x) damps outgoing waves (Sec. IV-C: "40-point deep
+ * ABC").  One step is
+ *
+ *     (1+b) u^{n+1} = 2 u^n - (1-b) u^{n-1} + (dt^2/m) (L u^n + s^n),
+ *
+ * b = gamma dt / 2, gamma = gamma_max * sum_a (depth_a / nbl)^2,
+ * gamma_max = 3 v_max ln(1000) / (2 nbl h); the ghost cells beyond the layer
+ * are zero (Sec. III "Access alignment": the halo is read-only).  Sources
+ * are injected and receivers interpolated with trilinear weights (Sec. III
+ * "Sparse data"); s^n = sum_src w q(t_n) / h^3 and rec[n] = I(u^n).
+ *
+ * Units: h in metres, dt in milliseconds, velocity in km/s, m in (ms/m)^2.
+ *
+ * Memory: every float array argument may be HOST or DEVICE memory on the
+ * grid's device; the library tells them apart with cudaPointerGetAttributes
+ * and stages host data through its own device buffers.  Point coordinate
+ * tables (fd_points.xyz) are host memory.  The caller owns every pointer it
+ * passes; the library never frees or retains them past the call.  The
+ * library owns all grid buffers (wavefields, model, checkpoints, tables).
+ *
+ * Ordering: calls run on the grid's stream and return after the work has
+ * completed, so the returned status reflects completion.  A grid must not be
+ * used from two threads at once.  Errors are returned as fd_status codes and
+ * never thrown across the ABI; fd_last_error() gives a thread-local message.
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fd_grid_s* fd_grid; /* opaque, library-owned */
+
+typedef enum {
+  FD_OK = 0,
+  FD_ERR_ARG = 1,       /* invalid argument (sizes, points outside the box) */
+  FD_ERR_CUDA = 2,      /* a CUDA call failed (message in fd_last_error) */
+  FD_ERR_OOM = 3,       /* device allocation failed */
+  FD_ERR_UNSTABLE = 4,  /* v_max dt / h above the stability limit */
+  FD_ERR_STATE = 5,     /* call out of order (e.g. no model set) */
+  FD_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out */
+  FD_ERR_NONFINITE = 7  /* NaN or Inf in the receiver data */
+} fd_status;
+
+/* kinds for fd_set_model */
+enum { FD_MODEL_VP_KMS = 0, /* P velocity in km/s */
+       FD_MODEL_M = 1 };    /* squared slowness m = 1/v^2 in (ms/m)^2 */
+
+/* regions for fd_set_wavefield / fd_get_wavefield */
+enum { FD_REGION_PHYSICAL = 0, /* nz*ny*nx physical cells */
+       FD_REGION_PADDED = 1 };  /* (nz+2nbl)*(ny+2nbl)*(nx+2nbl) cells */
+
+typedef struct {
+  int32_t nx, ny, nz;    /* physical cells, x fastest in every array */
+  double h;              /* grid spacing [m], the same on all axes */
+  int32_t space_order;   /* even, 2..16 */
+  int32_t nbl;           /* sponge cells added outside each face (>= 0) */
+  double dt;             /* time step [ms] */
+  int32_t nt;            /* number of steps run by fd_forward */
+  int32_t device;        /* CUDA device ordinal */
+  void* stream;          /* cudaStream_t to run on, or NULL for an own one */
+} fd_grid_desc;
+
+typedef struct {
+  int32_t n;             /* number of points */
+  const float* xyz;      /* host [n][3], metres from physical cell (0,0,0);
+                            each point must satisfy 0 <= x <= (nx-1) h etc. */
+} fd_points;
+
+typedef struct {
+  int32_t nx_pad, ny_pad, nz_pad; /* padded (physical + 2 nbl) extents */
+  int32_t pitch;                  /* floats between rows of device arrays */
+  int32_t tile_x, tile_y, zsplit; /* stencil tile chosen for this grid */
+  double v_max;                   /* from the model, km/s */
+  double cfl_limit;               /* largest stable v_max dt / h */
+  int64_t launches;               /* library kernels launched so far */
+  double step_ms;                 /* summed device time of profiled steps */
+  int64_t steps_timed;            /* steps inside that time */
+} fd_grid_info;
+
+/* Creates a grid; allocates the two wavefields and the model on `device`.
+ * Errors: FD_ERR_ARG (sizes), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_create_grid(const fd_grid_desc* desc, fd_grid* out);
+
+/* Frees every buffer of the grid.  NULL is accepted. */
+fd_status fd_destroy_grid(fd_grid grid);
+
+/* Sets the medium from nz*ny*nx physical values (`kind` FD_MODEL_*), padded
+ * into the sponge by edge replication, and resets the wavefields to zero.
+ * Errors: FD_ERR_ARG (non-positive or non-finite values), FD_ERR_UNSTABLE
+ * (v_max dt / h above the limit sqrt(4 / (3 S)), S = -c0 - 2 sum (-1)^j c_j). */
+fd_status fd_set_model(fd_grid grid, const float* data, int32_t kind);
+
+/* Forward modelling from rest (Eq. 1): runs desc.nt steps.
+ *   wavelet  [nt][src->n] source signatures q(t_n), t_n = n dt
+ *   rec_out  [nt][rec->n] receives I(u^n), n = 0..nt-1 (rec_out[0] = 0)
+ *   u_out    optional nz*ny*nx physical u^{nt} (NULL to skip)
+ * Errors: FD_ERR_STATE (no model), FD_ERR_ARG (points), FD_ERR_TIMEOUT,
+ * FD_ERR_NONFINITE (receiver data not finite). */
+fd_status fd_forward(fd_grid grid, const fd_points* src, const float* wavelet,
+                     const fd_points* rec, float* rec_out, float* u_out);
+
+/* Continues from the current wavefield state (u^{n0-1}, u^{n0}) for
+ * `nsteps` steps, using wavelet rows n0..n0+nsteps-1 (wavelet has
+ * n0+nsteps rows) and writing rec_out rows 0..nsteps-1 = I(u^{n0+t}).
+ * src, rec, wavelet and rec_out may be NULL for a source-free run. */
+fd_status fd_propagate(fd_grid grid, int32_t n0, int32_t nsteps,
+                       const fd_points* src, const float* wavelet,
+                       const fd_points* rec, float* rec_out);
+
+/* Replaces / reads the state (u^{n-1}, u^n); either pointer may be NULL. */
+fd_status fd_set_wavefield(fd_grid grid, const float* u_prev,
+                           const float* u_cur, int32_t region);
+fd_status fd_get_wavefield(fd_grid grid, float* u_prev, float* u_cur,
+                           int32_t region);
+
+/* Gradient of J = 1/2 sum_n ||I(u^n) - d_obs[n]||^2 with respect to the
+ * physical squared slowness m (nz*ny*nx floats), by the adjoint-state method
+ * with `n_checkpoints` stored states and recomputation between them.  The
+ * layer strength gamma_max is held fixed.  d_obs is [nt][rec->n]; the loss
+ * is written to *loss_out if not NULL.  Errors as fd_forward. */
+fd_status fd_adjoint_gradient(fd_grid grid, const fd_points* src,
+                              const float* wavelet, const fd_points* rec,
+                              const float* d_obs, int32_t n_checkpoints,
+                              float* grad_m, double* loss_out);
+
+/* Vector-Jacobian product: grad_m = (d rec / d m)^T grad_rec, with grad_rec
+ * [nt][rec->n] (the residual slot of the adjoint).  Used by autograd. */
+fd_status fd_backward(fd_grid grid, const fd_points* src, const float* wavelet,
+                      const fd_points* rec, const float* grad_rec,
+                      int32_t n_checkpoints, float* grad_m);
+
+/* Many independent shots (each its own grid, all with the same space order
+ * and nt) advanced together: each time step is one persistent launch over a
+ * shared {shot, tile} work list; the nt launches are captured in a CUDA
+ * graph when flags has FD_BATCH_GRAPH.  FD_BATCH_AUTOTUNE times the tile
+ * candidates once per (space order, window sizes) and caches the choice.
+ * All grids must be on the same device; the first grid's stream is used. */
+enum { FD_BATCH_GRAPH = 1, FD_BATCH_AUTOTUNE = 2 };
+typedef struct {
+  fd_grid grid;
+  const fd_points* src;
+  const float* wavelet;   /* [nt][src->n] */
+  const fd_points* rec;
+  float* rec_out;         /* [nt][rec->n] */
+} fd_shot;
+fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
+                           int32_t flags);
+
+/* Chooses the stencil tile (tile_x x tile_y points per CTA, z split into
+ * `zsplit` chunks).  Compiled tiles: 64x16, 128x8, 32x32, 64x8.
+ * Errors: FD_ERR_ARG for a tile that is not compiled or zsplit < 1. */
+fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t zsplit);
+
+/* Test hooks, host-side fault injection only:
+ *   FD_DEBUG_SKIP_PLANE  value z >= 0: the first step of the next run never
+ *                        issues the load of padded plane z, so the bounded
+ *                        waits for it run out and the call returns
+ *                        FD_ERR_TIMEOUT; -1 turns it off
+ *   FD_DEBUG_SPIN_LIMIT  clock cycles a device-side wait may take (> 0)
+ *   FD_DEBUG_NO_GRAPH    1: launch steps one by one instead of a CUDA graph
+ * Device allocations can be made to fail with FD_ERR_OOM by setting the
+ * environment variable FD_FAULT_ALLOC_AT=k (k-th allocation, 1-based). */
+enum { FD_DEBUG_SKIP_PLANE = 1, FD_DEBUG_SPIN_LIMIT = 2, FD_DEBUG_NO_GRAPH = 3 };
+fd_status fd_set_debug(fd_grid grid, int32_t key, int64_t value);
+
+/* Stencil weights.  FD_COEF_TAYLOR restores the order-2R Taylor weights;
+ * FD_COEF_UNIFORM takes c[0..R] (c[0] the centre weight per axis);
+ * FD_COEF_PER_CELL takes physical [nz][ny][nx][R] weights c_1..c_R per cell
+ * (c_0 = -2 sum c_j per cell), padded into the layer by edge replication;
+ * per-cell weights are compiled for space order 8 and forward runs only
+ * (fd_adjoint_gradient / fd_batch_forward then return FD_ERR_STATE).
+ * Errors: FD_ERR_ARG. */
+enum { FD_COEF_TAYLOR = 0, FD_COEF_UNIFORM = 1, FD_COEF_PER_CELL = 2 };
+fd_status fd_set_coefficients(fd_grid grid, const float* c, int32_t mode);
+
+/* ---- learned per-cell weights (no counterpart in the paper; follows the
+ * learned-discretisation idea of Bar-Sinai et al., PNAS 2019) -------------
+ * A 4 -> 64 -> 64 -> 8 ReLU network (FP32) maps x = [v dt/h, h/10 m,
+ * dt/1 ms, f/10 Hz] to outputs o_1..o_8; s_j = (o_j + o_{j+4})/2 and
+ * c_j = cT_j (1 + tanh(s_j)/2), j = 1..4, cT the SO 8 Taylor weights, so a
+ * zero output layer reproduces the plain stencil.  Parameters (5000 floats):
+ * W1[64][4] b1[64] W2[64][64] b2[64] W3[8][64] b3[8].  A training sample is
+ * 10 floats: x[4], T[4] (T_j = sum of the 6 neighbours at distance j minus
+ * 6 u), target y and weight w; loss (1/n) sum w (sum_j c_j T_j - y)^2. */
+#define FD_MLP_NPARAM 5000
+#define FD_MLP_SAMPLE 10
+typedef struct fd_mlp_s* fd_mlp;
+/* params: FD_MLP_NPARAM floats (host or device) or NULL for zeros. */
+fd_status fd_mlp_create(int32_t device, const float* params, fd_mlp* out);
+fd_status fd_mlp_destroy(fd_mlp net);
+fd_status fd_mlp_get_params(fd_mlp net, float* out);
+/* also resets the Adam state */
+fd_status fd_mlp_set_params(fd_mlp net, const float* in);
+/* loss and gradient over n samples ([n][FD_MLP_SAMPLE]); grad_out optional */
+fd_status fd_mlp_loss_grad(fd_mlp net, int64_t n, const float* samples, double* loss,
+                           float* grad_out);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient */
+fd_status fd_mlp_adam_step(fd_mlp net, float lr);
+/* `epochs` passes over the samples in mini-batches of `batch`, one Adam step
+ * per mini-batch; *loss_out = loss of the whole set at the end */
+fd_status fd_mlp_train(fd_mlp net, int64_t n, const float* samples, int32_t epochs,
+                       int32_t batch, float lr, double* loss_out);
+/* inference: coef_out[n][4] = c_1..c_4 of features[n][4] */
+fd_status fd_mlp_coefficients(fd_mlp net, int64_t n, const float* features, float* coef_out);
+/* per-cell weights of every cell of a space-order-8 grid from its model,
+ * computed by the network on the device (call after fd_set_model) */
+fd_status fd_set_learned_coefficients(fd_grid grid, fd_mlp net, double f_hz);
+/* Training-data helpers.  fd_sample_stencil writes, for each padded cell
+ * (x, y, z) of cells[n][3], the current wavefield at the cell and at
+ * distances j*stride (j = 1..radius) along -x, +x, -y, +y, -z, +z:
+ * out[n][1 + 6 radius]; outside the grid reads 0.  fd_mlp_make_samples
+ * turns three such arrays (radius 4; coarse times t-dt, t, t+dt) and the
+ * velocity at each cell into samples: x as above, T_j from `cur`,
+ * y = (next - 2 cur + prev) / C^2 with C = v dt / h at the centre, and
+ * w = 1 / (scale + mean square of the cur stencil).  Device arrays only. */
+fd_status fd_sample_stencil(fd_grid grid, int32_t n, const int32_t* cells, int32_t stride,
+                            int32_t radius, float* out);
+fd_status fd_mlp_make_samples(int32_t n, const float* prev, const float* cur, const float* next,
+                              const float* vel, double h, double dt, double f_hz, double scale,
+                              float* out);
+
+/* Diagnostics. */
+fd_status fd_get_info(fd_grid grid, fd_grid_info* info);
+/* When enabled, fd_forward / fd_propagate / fd_batch_forward record CUDA
+ * events around the step launches on the grid's stream and add the time to
+ * fd_grid_info.step_ms. */
+fd_status fd_set_profiling(fd_grid grid, int32_t enabled);
+/* Library-wide count of kernel launches issued so far. */
+int64_t fd_launch_count(void);
+
+const char* fd_status_string(fd_status status);
+const char* fd_last_error(void); /* thread-local; "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_H */

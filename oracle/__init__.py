@@ -81,6 +81,8 @@ def _load():
                                             ctypes.c_int32, _D, _D, _D, _D,
                                             _D, _D]
         lib.or_adjoint_gradient.restype = ctypes.c_int32
+        lib.or_step_points.argtypes = [G, _D, ctypes.c_double, _D, _D, _D,
+                                       ctypes.c_int64, _I64, _D]
         _lib = lib
     return _lib
 
@@ -190,6 +192,18 @@ def step(g: Grid, m_pad, b, u_prev, u_cur, *, coef=None, percell=None,
                     _p(_f64(percell)), _p(_f64(u_prev)), _p(_f64(u_cur)), ns,
                     si.ctypes.data_as(_I64), _p(sv), _p(L), _p(out), _p(e))
     return out, e
+
+
+def step_points(g: Grid, m_phys, vmax: float, u_prev, u_cur, idx, coef=None):
+    """One source-free step evaluated only at padded flat indices ``idx``."""
+    coef = fd_coefficients(g.R) if coef is None else _f64(coef)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(len(idx))
+    gc = g.c()
+    _load().or_step_points(ctypes.byref(gc), _p(_f64(m_phys)), float(vmax), _p(coef),
+                           _p(_f64(u_prev)), _p(_f64(u_cur)), len(idx),
+                           idx.ctypes.data_as(_I64), _p(out))
+    return out
 
 
 def heat_step(g: Grid, u) -> np.ndarray:

@@ -422,3 +422,50 @@ done:
   free(z0); free(z1); free(z2); free(L); free(gpad); free(rp);
   return rcode;
 }
+
+/*
+ * The damped leapfrog update (same definition as or_step) evaluated only at
+ * the listed padded cells, for checking sampled outputs of grids too large
+ * to step on the CPU.  m_phys is the physical model; v_max sets the layer.
+ * No source term.
+ */
+void or_step_points(const or_grid* g, const double* m_phys, double vmax,
+                    const double* coef, const double* u_prev, const double* u_cur,
+                    int64_t npts, const int64_t* idx, double* out) {
+  int64_t N[3];
+  padded_dims(g, N);
+  int R = g->R;
+  double ih2 = 1.0 / (g->h * g->h);
+  double dt2 = g->dt * g->dt;
+  double gmax = 0.0;
+  if (g->nbl > 0)
+    gmax = 3.0 * vmax * log(1.0 / g->rc) / (2.0 * g->nbl * g->h);
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < npts; ++s) {
+    int64_t id = idx[s];
+    int64_t p[3] = {id % N[0], (id / N[0]) % N[1], id / (N[0] * N[1])};
+    double acc = 0.0, damp = 0.0;
+    int64_t q[3] = {0, 0, 0};
+    for (int a = 0; a < g->dims; ++a) {
+      acc += coef[0] * u_cur[id];
+      for (int r = 1; r <= R; ++r)
+        acc += coef[r] * (neighbour(g, N, u_cur, p[0], p[1], p[2], a, r) +
+                          neighbour(g, N, u_cur, p[0], p[1], p[2], a, -r));
+      double lo = (double)(g->nbl - p[a]);
+      double hi = (double)(p[a] - (g->n[a] + g->nbl - 1));
+      double d = 0.0;
+      if (lo > d) d = lo;
+      if (hi > d) d = hi;
+      if (g->nbl > 0) d /= g->nbl;
+      damp += d * d;
+      int64_t v = p[a] - g->nbl;
+      if (v < 0) v = 0;
+      if (v > g->n[a] - 1) v = g->n[a] - 1;
+      q[a] = v;
+    }
+    double m = m_phys[q[0] + (int64_t)g->n[0] * (q[1] + (int64_t)g->n[1] * q[2])];
+    double b = gmax * damp * g->dt / 2.0;
+    double e = dt2 / m * acc * ih2;
+    out[s] = (2.0 * u_cur[id] - (1.0 - b) * u_prev[id] + e) / (1.0 + b);
+  }
+}

@@ -1,0 +1,94 @@
+// Internal types shared by the CUDA translation units of libfd.so.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fd {
+
+constexpr int kMaxR = 8;  // space order up to 16
+
+// One source node: padded z, tile-local x/y of the node, scaled weight and the
+// column of the value table (wavelet or residual) that feeds it.
+struct InjEntry {
+  int32_t z;
+  int16_t lx, ly;
+  float w;
+  int32_t col;
+};
+
+// One receiver: padded z of its floor node, tile-local floor x/y, the three
+// fractional offsets and its output column.
+struct RecEntry {
+  int32_t z;
+  int16_t lx, ly;
+  float fx, fy, fz;
+  int32_t col;
+};
+
+enum StepMode : int {
+  kModeForward = 0,    // u^{n+1} only
+  kModeStoreE = 1,     // also e = (dt^2/m)(L u + s) for the imaging condition
+  kModeAdjoint = 2,    // also grad -= u_cur * e_in / dt^2 (u_cur = z^{n+1})
+  kModePerCell = 3     // forward with per-cell weights c_1..c_R (space order 8)
+};
+
+// Everything one launch of the step kernel needs besides the tensor maps.
+struct StepArgs {
+  int32_t Nx, Ny, Nz;      // padded extents
+  int32_t pitch;           // floats per row of every device array
+  int32_t nbl, nx, ny, nz; // layer width and physical extents
+  int32_t tiles_x, tiles_y, zsplit, zlen;
+  float bscale;            // gamma_max * dt / 2 / nbl^2
+  float c[kMaxR + 1];      // second-derivative weights c_0..c_R
+  float* out;              // u^{n+1}: the u^{n-1} buffer, updated in place
+  const int32_t* inj_start;  // [tiles_x*tiles_y + 1] or nullptr
+  const InjEntry* inj;
+  const float* inj_val;      // [step][inj_ncol]
+  int32_t inj_ncol;
+  const int32_t* rec_start;  // [tiles_x*tiles_y + 1] or nullptr
+  const RecEntry* recs;
+  float* rec_out;            // [step][rec_ncol]
+  int32_t rec_ncol;
+  int32_t inj_row;           // row of inj_val read by this launch
+  int32_t rec_row;           // row of rec_out written by this launch
+  float* e_out;              // kModeStoreE
+  const float* e_in;         // kModeAdjoint
+  float* grad;               // kModeAdjoint (padded, pitched)
+  float inv_dt2;
+  int32_t* err;              // device error word (bit 0: wait timed out)
+  long long spin_limit;      // clock cycles before a wait gives up
+  int32_t debug_skip_plane;  // test hook: never issue this plane's load (-1)
+};
+
+// One shot of a batched launch (device memory, 64-byte aligned for the maps).
+struct BatchShot {
+  CUtensorMap halo[2];  // u^n with halo, per buffer
+  CUtensorMap tile[2];  // u^{n-1} tiles, per buffer
+  CUtensorMap A;
+  StepArgs args;        // per-shot constants; rows are set per launch
+  float* u[2];
+};
+
+struct TileShape {
+  int tx, ty, pf;   // threads in x (4 points each), rows, prefetch depth
+  int zsplit;       // z chunks per column
+};
+
+// Per-radius launchers, specialised in fd_step_r<R>.cu.
+template <int R>
+cudaError_t launch_step_r(const TileShape& t, int mode, const CUtensorMap& halo,
+                          const CUtensorMap& tile_prev, const CUtensorMap& tileA,
+                          const CUtensorMap& tileC, const StepArgs& a, cudaStream_t s);
+template <int R>
+cudaError_t launch_batch_r(const TileShape& t, const BatchShot* shots, const int4* work,
+                           int nwork, int* counter, int step, int grid, cudaStream_t s);
+template <int R>
+int batch_blocks_per_sm_r(const TileShape& t);
+template <int R>
+size_t smem_r(const TileShape& t);
+template <int R>
+int regs_r(const TileShape& t);
+
+}  // namespace fd

@@ -1,0 +1,971 @@
+// Host runtime of libfd.so: the C ABI declared in include/fd.h.
+//
+// Owns the device state of a grid (two wavefields, the model term A, the
+// per-tile source/receiver tables, checkpoints), builds the TMA tensor maps,
+// captures the time loop in a CUDA graph and maps every failure to a status
+// code with a thread-local message.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/fd.h"
+#include "fd_aux.h"
+#include "fd_internal.h"
+#include "fd_mlp.h"
+#include "fd_runtime.h"
+
+namespace fd {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static thread_local std::string t_err;
+
+fd_status fail(fd_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return st;
+}
+
+fd_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(FD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(FD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void clear_error() { t_err.clear(); }
+
+// --------------------------------------------------------------------------
+// allocation with a host-side failure-injection hook: FD_FAULT_ALLOC_AT=k makes
+// the k-th device allocation of the process (1-based) fail with OOM.
+// --------------------------------------------------------------------------
+static std::atomic<long long> g_alloc_count{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  const long long k = g_alloc_count.fetch_add(1) + 1;
+  const char* env = getenv("FD_FAULT_ALLOC_AT");
+  if (env && atoll(env) == k) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t DevBuf::ensure(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = dev_alloc(&p, bytes);
+  if (e == cudaSuccess) cap = bytes;
+  return e;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// --------------------------------------------------------------------------
+// tensor maps
+// --------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+fd_status make_map(CUtensorMap* m, const float* base, int Nx, int Ny, int Nz,
+                   int pitch, int bx, int by) {
+  auto fn = encode_fn();
+  if (!fn) return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[3] = {(cuuint64_t)Nx, (cuuint64_t)Ny, (cuuint64_t)Nz};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * Ny};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for box %dx%d", (int)r,
+                bx, by);
+  return FD_OK;
+}
+
+int radius_halo_x(int R) { return ((R + 3) / 4) * 4; }
+
+fd_status build_field_maps(fd_grid g, Fields& f) {
+  const int bx = 4 * g->shape.tx, by = g->shape.ty;
+  const int W = bx + 2 * radius_halo_x(g->R), H = by + 2 * g->R;
+  for (int b = 0; b < 2; ++b) {
+    if (!f.u[b]) continue;
+    fd_status st = make_map(&f.halo[b], f.u[b], g->Nx, g->Ny, g->Nz, g->pitch, W, H);
+    if (st) return st;
+    st = make_map(&f.tile[b], f.u[b], g->Nx, g->Ny, g->Nz, g->pitch, bx, by);
+    if (st) return st;
+  }
+  return FD_OK;
+}
+
+fd_status build_maps(fd_grid g) {
+  fd_status st = build_field_maps(g, g->F);
+  if (!st) st = build_field_maps(g, g->Z);
+  if (st) return st;
+  const int bx = 4 * g->shape.tx, by = g->shape.ty;
+  st = make_map(&g->mapA, g->A, g->Nx, g->Ny, g->Nz, g->pitch, bx, by);
+  if (st) return st;
+  if (g->coef)  // the R coefficient fields stacked along z
+    return make_map(&g->mapC, g->coef, g->Nx, g->Ny, g->R * g->Nz, g->pitch, bx, by);
+  return FD_OK;
+}
+
+// --------------------------------------------------------------------------
+// dispatch over radius
+// --------------------------------------------------------------------------
+cudaError_t launch_step(int R, const TileShape& t, int mode, const CUtensorMap& h,
+                        const CUtensorMap& p, const CUtensorMap& A, const CUtensorMap& C,
+                        const StepArgs& a, cudaStream_t s) {
+  count_launch();
+  switch (R) {
+    case 1: return launch_step_r<1>(t, mode, h, p, A, C, a, s);
+    case 2: return launch_step_r<2>(t, mode, h, p, A, C, a, s);
+    case 3: return launch_step_r<3>(t, mode, h, p, A, C, a, s);
+    case 4: return launch_step_r<4>(t, mode, h, p, A, C, a, s);
+    case 5: return launch_step_r<5>(t, mode, h, p, A, C, a, s);
+    case 6: return launch_step_r<6>(t, mode, h, p, A, C, a, s);
+    case 7: return launch_step_r<7>(t, mode, h, p, A, C, a, s);
+    case 8: return launch_step_r<8>(t, mode, h, p, A, C, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t step_smem(int R, const TileShape& t) {
+  switch (R) {
+    case 1: return smem_r<1>(t);
+    case 2: return smem_r<2>(t);
+    case 3: return smem_r<3>(t);
+    case 4: return smem_r<4>(t);
+    case 5: return smem_r<5>(t);
+    case 6: return smem_r<6>(t);
+    case 7: return smem_r<7>(t);
+    case 8: return smem_r<8>(t);
+  }
+  return 0;
+}
+
+const TileShape kShapes[kNumShapes] = {
+    {16, 16, 2, 1}, {32, 8, 2, 1}, {8, 32, 2, 1}, {16, 8, 3, 1}};
+
+// Default tile: 64x16 for the narrow stencils, 128x8 when the halo is wide.
+TileShape default_shape(int R, int Nx, int Ny, int Nz) {
+  (void)Nx;
+  (void)Ny;
+  (void)Nz;
+  TileShape t = kShapes[0];
+  if (R >= 6) t = kShapes[1];
+  return t;
+}
+
+void set_shape(fd_grid g, TileShape t) {
+  const int bx = 4 * t.tx, by = t.ty;
+  g->shape = t;
+  g->tiles_x = (g->Nx + bx - 1) / bx;
+  g->tiles_y = (g->Ny + by - 1) / by;
+  if (t.zsplit < 1) g->shape.zsplit = 1;
+  g->zlen = (g->Nz + g->shape.zsplit - 1) / g->shape.zsplit;
+  g->graph_valid = false;
+}
+
+// FD weights: c_j = 2(-1)^{j+1}(R!)^2/(j^2 (R-j)!(R+j)!), c_0 = -2 sum c_j.
+void fd_weights(int R, double* c) {
+  double sum = 0.0;
+  for (int j = 1; j <= R; ++j) {
+    double ratio = 1.0;
+    for (int k = 1; k <= j; ++k) ratio *= double(R - k + 1) / double(R + k);
+    c[j] = ((j & 1) ? 2.0 : -2.0) * ratio / (double(j) * j);
+    sum += c[j];
+  }
+  c[0] = -2.0 * sum;
+}
+
+// Largest stable v dt / h of the 3D leapfrog: sqrt(4 / (3 S)) with S the
+// magnitude of the 1D stencil symbol at the Nyquist wavenumber.
+double cfl_limit(const double* c, int R) {
+  double S = -c[0];
+  for (int j = 1; j <= R; ++j) S -= 2.0 * ((j & 1) ? -c[j] : c[j]);
+  return sqrt(4.0 / (3.0 * S));
+}
+
+// --------------------------------------------------------------------------
+// source / receiver tables
+// --------------------------------------------------------------------------
+struct PointCell {
+  int i0[3];
+  double f[3];
+};
+
+static fd_status locate(fd_grid g, const float* xyz, PointCell* pc) {
+  const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+  for (int a = 0; a < 3; ++a) {
+    const double s = double(xyz[a]) / g->d.h;
+    if (!(s >= 0.0) || s > double(n[a] - 1))
+      return fail(FD_ERR_ARG, "point (%g, %g, %g) outside the physical box", xyz[0], xyz[1],
+                  xyz[2]);
+    const double fl = floor(s);
+    pc->i0[a] = int(fl) + g->d.nbl;
+    pc->f[a] = s - fl;
+  }
+  return FD_OK;
+}
+
+// Trilinear injection entries of every point, scaled by `scale`, grouped per
+// tile and sorted by z within a tile.
+fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
+                          std::vector<int32_t>& start, std::vector<InjEntry>& out) {
+  const int bx = 4 * g->shape.tx, by = g->shape.ty;
+  const int ntiles = g->tiles_x * g->tiles_y;
+  std::vector<std::pair<int, InjEntry>> ent;
+  for (int p = 0; p < (pts ? pts->n : 0); ++p) {
+    PointCell pc;
+    fd_status st = locate(g, pts->xyz + 3 * p, &pc);
+    if (st) return st;
+    for (int c = 0; c < 8; ++c) {
+      int node[3];
+      double w = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        const int hi = (c >> a) & 1;
+        node[a] = pc.i0[a] + hi;
+        w *= hi ? pc.f[a] : 1.0 - pc.f[a];
+      }
+      if (w == 0.0) continue;
+      if (node[0] >= g->Nx || node[1] >= g->Ny || node[2] >= g->Nz) continue;
+      InjEntry e;
+      e.z = node[2];
+      e.lx = int16_t(node[0] % bx);
+      e.ly = int16_t(node[1] % by);
+      e.w = float(w * scale);
+      e.col = p;
+      ent.push_back({(node[1] / by) * g->tiles_x + node[0] / bx, e});
+    }
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
+    return a.first != b.first ? a.first < b.first : a.second.z < b.second.z;
+  });
+  start.assign(ntiles + 1, 0);
+  out.clear();
+  for (auto& e : ent) {
+    start[e.first + 1]++;
+    out.push_back(e.second);
+  }
+  for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
+  return FD_OK;
+}
+
+fd_status build_receivers(fd_grid g, const fd_points* pts, std::vector<int32_t>& start,
+                          std::vector<RecEntry>& out) {
+  const int bx = 4 * g->shape.tx, by = g->shape.ty;
+  const int ntiles = g->tiles_x * g->tiles_y;
+  std::vector<std::pair<int, RecEntry>> ent;
+  for (int p = 0; p < (pts ? pts->n : 0); ++p) {
+    PointCell pc;
+    fd_status st = locate(g, pts->xyz + 3 * p, &pc);
+    if (st) return st;
+    RecEntry e;
+    e.z = pc.i0[2];
+    e.lx = int16_t(pc.i0[0] % bx);
+    e.ly = int16_t(pc.i0[1] % by);
+    e.fx = float(pc.f[0]);
+    e.fy = float(pc.f[1]);
+    e.fz = float(pc.f[2]);
+    e.col = p;
+    ent.push_back({(pc.i0[1] / by) * g->tiles_x + pc.i0[0] / bx, e});
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
+    return a.first != b.first ? a.first < b.first : a.second.z < b.second.z;
+  });
+  start.assign(ntiles + 1, 0);
+  out.clear();
+  for (auto& e : ent) {
+    start[e.first + 1]++;
+    out.push_back(e.second);
+  }
+  for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
+  return FD_OK;
+}
+
+template <class T>
+static fd_status upload(fd_grid g, DevBuf& buf, const std::vector<T>& v) {
+  cudaError_t e = buf.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+  if (e) return cuda_fail(e, "table allocation");
+  if (!v.empty()) {
+    e = cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                        g->stream);
+    if (e) return cuda_fail(e, "table upload");
+  }
+  return FD_OK;
+}
+
+fd_status upload_tables(fd_grid g, const fd_points* src, double src_scale,
+                        const fd_points* rec, Tables& t) {
+  std::vector<int32_t> is, rs;
+  std::vector<InjEntry> ie;
+  std::vector<RecEntry> re;
+  fd_status st = build_injection(g, src, src_scale, is, ie);
+  if (st) return st;
+  st = build_receivers(g, rec, rs, re);
+  if (st) return st;
+  if ((st = upload(g, t.inj_start, is))) return st;
+  if ((st = upload(g, t.inj, ie))) return st;
+  if ((st = upload(g, t.rec_start, rs))) return st;
+  if ((st = upload(g, t.recs, re))) return st;
+  t.n_inj = int(ie.size());
+  t.n_rec = int(re.size());
+  // keep the uploads ordered before the host vectors go away
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "table upload");
+  return FD_OK;
+}
+
+// Device view of a caller array: the pointer itself if it is device memory,
+// else a staging buffer (filled from the host when `in`).
+fd_status stage_in(fd_grid g, DevBuf& buf, const float* p, size_t n, const float** out) {
+  if (!p || n == 0) {
+    *out = nullptr;
+    return FD_OK;
+  }
+  if (is_device_ptr(p)) {
+    *out = p;
+    return FD_OK;
+  }
+  cudaError_t e = buf.ensure(n * sizeof(float));
+  if (e) return cuda_fail(e, "staging allocation");
+  e = cudaMemcpyAsync(buf.p, p, n * sizeof(float), cudaMemcpyHostToDevice, g->stream);
+  if (e) return cuda_fail(e, "host to device copy");
+  *out = static_cast<const float*>(buf.p);
+  return FD_OK;
+}
+
+fd_status stage_out(fd_grid g, DevBuf& buf, float* p, size_t n, float** out) {
+  if (!p || n == 0) {
+    *out = nullptr;
+    return FD_OK;
+  }
+  if (is_device_ptr(p)) {
+    *out = p;
+    return FD_OK;
+  }
+  cudaError_t e = buf.ensure(n * sizeof(float));
+  if (e) return cuda_fail(e, "staging allocation");
+  *out = static_cast<float*>(buf.p);
+  return FD_OK;
+}
+
+fd_status finish_out(fd_grid g, float* host, const float* dev, size_t n) {
+  if (!host || host == dev || n == 0) return FD_OK;
+  cudaError_t e =
+      cudaMemcpyAsync(host, dev, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream);
+  if (e) return cuda_fail(e, "device to host copy");
+  return FD_OK;
+}
+
+// --------------------------------------------------------------------------
+// time loop
+// --------------------------------------------------------------------------
+StepArgs base_args(fd_grid g) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Nx = g->Nx;
+  a.Ny = g->Ny;
+  a.Nz = g->Nz;
+  a.pitch = g->pitch;
+  a.nbl = g->d.nbl;
+  a.nx = g->d.nx;
+  a.ny = g->d.ny;
+  a.nz = g->d.nz;
+  a.tiles_x = g->tiles_x;
+  a.tiles_y = g->tiles_y;
+  a.zsplit = g->shape.zsplit;
+  a.zlen = g->zlen;
+  a.bscale = g->bscale;
+  for (int j = 0; j <= kMaxR; ++j) a.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
+  a.err = g->d_err;
+  a.spin_limit = g->spin_limit;
+  a.debug_skip_plane = -1;
+  return a;
+}
+
+fd_status run_steps(fd_grid g, const RunSpec& rs) {
+  if (rs.nsteps <= 0) return FD_OK;
+  cudaError_t e;
+  Fields& F = *rs.f;
+  const bool use_graph = rs.allow_graph && rs.nsteps >= 2 && !g->no_graph;
+  GraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.spec = rs;
+  key.cur = F.cur;
+  key.shape = g->shape;
+  key.skip = g->debug_skip_plane + (g->percell ? 1 << 20 : 0);
+  key.bscale = g->bscale;
+  const bool reuse = use_graph && g->graph_valid && memcmp(&key, &g->gkey, sizeof(key)) == 0;
+  if (g->profiling) cudaEventRecord(g->ev0, g->stream);
+  if (reuse) {
+    e = cudaGraphLaunch(g->gexec, g->stream);
+    if (e) return cuda_fail(e, "graph launch");
+    count_launch(rs.nsteps);
+    F.cur = (F.cur + rs.nsteps) & 1;
+  } else {
+    if (use_graph) {
+      if (g->graph_valid) {
+        cudaGraphExecDestroy(g->gexec);
+        g->graph_valid = false;
+      }
+      e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed);
+      if (e) return cuda_fail(e, "stream capture");
+    }
+    const int cur0 = F.cur;
+    long long before = g_launches.load();
+    for (int t = 0; t < rs.nsteps; ++t) {
+      const int cur = (cur0 + t) & 1, prev = cur ^ 1;
+      StepArgs a = base_args(g);
+      a.out = F.u[prev];
+      a.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
+      if (rs.inj_val) {
+        a.inj_start = rs.inj_start;
+        a.inj = rs.inj;
+        a.inj_val = rs.inj_val;
+        a.inj_ncol = rs.inj_ncol;
+        a.inj_row = rs.inj_row0 + rs.inj_row_step * t;
+      }
+      if (rs.rec_out) {
+        a.rec_start = rs.rec_start;
+        a.recs = rs.recs;
+        a.rec_out = rs.rec_out;
+        a.rec_ncol = rs.rec_ncol;
+        a.rec_row = rs.rec_row0 + rs.rec_row_step * t;
+      }
+      if (rs.mode == kModeStoreE) a.e_out = rs.e_base + size_t(t) * g->ncell;
+      if (rs.mode == kModeAdjoint) {
+        a.e_in = rs.e_base + size_t(rs.e_idx0 + rs.e_idx_step * t) * g->ncell;
+        a.grad = rs.grad;
+        a.inv_dt2 = float(1.0 / (g->d.dt * g->d.dt));
+      }
+      const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
+      e = launch_step(g->R, g->shape, mode, F.halo[cur], F.tile[prev], g->mapA,
+                      g->coef ? g->mapC : g->mapA, a, g->stream);
+      if (e) {
+        if (use_graph) {
+          cudaGraph_t dummy;
+          cudaStreamEndCapture(g->stream, &dummy);
+          if (dummy) cudaGraphDestroy(dummy);
+        }
+        return cuda_fail(e, "step launch");
+      }
+    }
+    F.cur = (cur0 + rs.nsteps) & 1;
+    if (use_graph) {
+      // count the graph's launches when it runs, not at capture
+      g_launches.store(before);
+      cudaGraph_t graph;
+      e = cudaStreamEndCapture(g->stream, &graph);
+      if (e) return cuda_fail(e, "end capture");
+      e = cudaGraphInstantiate(&g->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e) return cuda_fail(e, "graph instantiate");
+      g->graph_valid = true;
+      key.cur = cur0;
+      g->gkey = key;
+      e = cudaGraphLaunch(g->gexec, g->stream);
+      if (e) return cuda_fail(e, "graph launch");
+      count_launch(rs.nsteps);
+    }
+  }
+  if (g->profiling) {
+    cudaEventRecord(g->ev1, g->stream);
+    e = cudaEventSynchronize(g->ev1);
+    if (e) return cuda_fail(e, "profiling event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    g->step_ms += ms;
+    g->steps_timed += rs.nsteps;
+  }
+  return FD_OK;
+}
+
+fd_status check_device_error(fd_grid g) {
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "stream synchronize");
+  int h = 0;
+  e = cudaMemcpy(&h, g->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(e, "error word read");
+  if (h) {
+    cudaMemset(g->d_err, 0, sizeof(int));
+    return fail(FD_ERR_TIMEOUT, "a device-side wait ran out (error word %d)", h);
+  }
+  return FD_OK;
+}
+
+fd_status check_finite(fd_grid g, const float* dev, size_t n) {
+  int h = 0;
+  cudaError_t e = count_nonfinite(dev, n, g->d_err + 1, &h, g->stream);
+  if (e) return cuda_fail(e, "finite check");
+  if (h) return fail(FD_ERR_NONFINITE, "%d receiver samples are NaN or Inf", h);
+  return FD_OK;
+}
+
+// Copy between the padded pitched wavefield and a dense caller array.
+fd_status copy_field(fd_grid g, float* dev_field, void* user, int region, bool to_user) {
+  cudaMemcpy3DParms p;
+  memset(&p, 0, sizeof(p));
+  const bool phys = region == FD_REGION_PHYSICAL;
+  const int ex = phys ? g->d.nx : g->Nx, ey = phys ? g->d.ny : g->Ny,
+            ez = phys ? g->d.nz : g->Nz;
+  const int off = phys ? g->d.nbl : 0;
+  cudaPitchedPtr dev = make_cudaPitchedPtr(dev_field, size_t(g->pitch) * 4, g->Nx * 4, g->Ny);
+  cudaPitchedPtr usr = make_cudaPitchedPtr(user, size_t(ex) * 4, ex * 4, ey);
+  if (to_user) {
+    p.srcPtr = dev;
+    p.srcPos = make_cudaPos(size_t(off) * 4, off, off);
+    p.dstPtr = usr;
+  } else {
+    p.srcPtr = usr;
+    p.dstPtr = dev;
+    p.dstPos = make_cudaPos(size_t(off) * 4, off, off);
+  }
+  p.extent = make_cudaExtent(size_t(ex) * 4, ey, ez);
+  p.kind = cudaMemcpyDefault;
+  cudaError_t e = cudaMemcpy3DAsync(&p, g->stream);
+  if (e) return cuda_fail(e, "wavefield copy");
+  return FD_OK;
+}
+
+}  // namespace fd
+
+using namespace fd;
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+const char* fd_status_string(fd_status s) {
+  switch (s) {
+    case FD_OK: return "ok";
+    case FD_ERR_ARG: return "invalid argument";
+    case FD_ERR_CUDA: return "CUDA error";
+    case FD_ERR_OOM: return "out of device memory";
+    case FD_ERR_UNSTABLE: return "time step above the stability limit";
+    case FD_ERR_STATE: return "call out of order";
+    case FD_ERR_TIMEOUT: return "device-side wait timed out";
+    case FD_ERR_NONFINITE: return "non-finite receiver data";
+  }
+  return "unknown status";
+}
+
+const char* fd_last_error(void) { return t_err.c_str(); }
+
+int64_t fd_launch_count(void) { return g_launches.load(); }
+
+fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
+  clear_error();
+  if (!d || !out) return fail(FD_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+    return fail(FD_ERR_ARG, "grid sizes must be positive");
+  if (!(d->h > 0.0) || !(d->dt > 0.0)) return fail(FD_ERR_ARG, "h and dt must be positive");
+  if (d->space_order < 2 || d->space_order > 16 || (d->space_order & 1))
+    return fail(FD_ERR_ARG, "space_order must be even, 2..16");
+  if (d->nbl < 0 || d->nt < 0) return fail(FD_ERR_ARG, "nbl and nt must be >= 0");
+  const long long Nx = d->nx + 2LL * d->nbl, Ny = d->ny + 2LL * d->nbl,
+                  Nz = d->nz + 2LL * d->nbl;
+  if (Nx > (1 << 24) || Ny > 65535 || Nz > 65535)
+    return fail(FD_ERR_ARG, "padded grid too large for the launch shape");
+  cudaError_t e = cudaSetDevice(d->device);
+  if (e) return cuda_fail(e, "cudaSetDevice");
+
+  fd_grid g = new fd_grid_s();
+  g->d = *d;
+  g->R = d->space_order / 2;
+  g->Nx = int(Nx);
+  g->Ny = int(Ny);
+  g->Nz = int(Nz);
+  g->pitch = int((Nx + 31) / 32 * 32);
+  g->ncell = size_t(g->pitch) * g->Ny * g->Nz;
+  fd_weights(g->R, g->c);
+  g->cfl = cfl_limit(g->c, g->R);
+  g->spin_limit = 4000000000LL;  // ~2 s at 2 GHz
+  if (const char* s = getenv("FD_SPIN_LIMIT")) g->spin_limit = atoll(s);
+  set_shape(g, default_shape(g->R, g->Nx, g->Ny, g->Nz));
+
+  fd_status st = FD_OK;
+  if (d->stream) {
+    g->stream = static_cast<cudaStream_t>(d->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e) st = cuda_fail(e, "stream create");
+    g->own_stream = true;
+  }
+  for (int b = 0; b < 2 && !st; ++b) {
+    e = dev_alloc(reinterpret_cast<void**>(&g->F.u[b]), g->ncell * 4);
+    if (e) st = cuda_fail(e, "wavefield allocation");
+  }
+  if (!st) {
+    e = dev_alloc(reinterpret_cast<void**>(&g->A), g->ncell * 4);
+    if (e) st = cuda_fail(e, "model allocation");
+  }
+  if (!st) {
+    e = dev_alloc(reinterpret_cast<void**>(&g->d_err), 64);
+    if (e) st = cuda_fail(e, "status allocation");
+  }
+  if (!st) {
+    e = cudaMemsetAsync(g->d_err, 0, 64, g->stream);
+    for (int b = 0; b < 2 && !e; ++b) e = cudaMemsetAsync(g->F.u[b], 0, g->ncell * 4, g->stream);
+    if (!e) e = cudaMemsetAsync(g->A, 0, g->ncell * 4, g->stream);
+    if (!e) e = cudaEventCreate(&g->ev0);
+    if (!e) e = cudaEventCreate(&g->ev1);
+    if (!e) e = cudaStreamSynchronize(g->stream);
+    if (e) st = cuda_fail(e, "grid initialisation");
+  }
+  if (!st) st = build_maps(g);
+  if (st) {
+    std::string keep = t_err;
+    fd_destroy_grid(g);
+    t_err = keep;
+    return st;
+  }
+  *out = g;
+  return FD_OK;
+}
+
+fd_status fd_destroy_grid(fd_grid g) {
+  if (!g) return FD_OK;
+  cudaSetDevice(g->d.device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->graph_valid) cudaGraphExecDestroy(g->gexec);
+  for (int b = 0; b < 2; ++b) {
+    if (g->F.u[b]) cudaFree(g->F.u[b]);
+    if (g->Z.u[b]) cudaFree(g->Z.u[b]);
+  }
+  if (g->A) cudaFree(g->A);
+  if (g->coef) cudaFree(g->coef);
+  if (g->d_err) cudaFree(g->d_err);
+  for (DevBuf* b : {&g->tab.inj_start, &g->tab.inj, &g->tab.rec_start, &g->tab.recs,
+                    &g->tab_adj.inj_start, &g->tab_adj.inj, &g->tab_adj.rec_start,
+                    &g->tab_adj.recs,
+                    &g->stage_val, &g->stage_rec, &g->stage_aux, &g->ckpt, &g->ebuf,
+                    &g->gpad, &g->resid, &g->recbuf})
+    b->release();
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return FD_OK;
+}
+
+fd_status fd_set_model(fd_grid g, const float* data, int32_t kind) {
+  clear_error();
+  if (!g || !data) return fail(FD_ERR_ARG, "null argument");
+  if (kind != FD_MODEL_VP_KMS && kind != FD_MODEL_M) return fail(FD_ERR_ARG, "bad model kind");
+  cudaSetDevice(g->d.device);
+  const size_t np = size_t(g->d.nx) * g->d.ny * g->d.nz;
+  const float* dev = data;
+  cudaError_t e;
+  if (!is_device_ptr(data)) {
+    // stage through the second wavefield (it is reset below)
+    e = cudaMemcpyAsync(g->F.u[1], data, np * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e) return cuda_fail(e, "model upload");
+    dev = g->F.u[1];
+  }
+  float vmin = 0, vmax = 0;
+  int nbad = 0;
+  e = model_stats(dev, np, kind, &vmin, &vmax, &nbad,
+                  reinterpret_cast<unsigned int*>(g->d_err + 4), g->stream);
+  if (e) return cuda_fail(e, "model statistics");
+  if (nbad) return fail(FD_ERR_ARG, "%d model values are not positive and finite", nbad);
+  const double courant = double(vmax) * g->d.dt / g->d.h;
+  if (courant > g->cfl)
+    return fail(FD_ERR_UNSTABLE, "v_max dt / h = %.4f exceeds the limit %.4f for SO %d",
+                courant, g->cfl, g->d.space_order);
+  e = model_to_A(dev, kind, g->d.nx, g->d.ny, g->d.nz, g->d.nbl, g->Nx, g->Ny, g->Nz,
+                 g->pitch, g->d.dt * g->d.dt / (g->d.h * g->d.h), g->A, g->stream);
+  if (e) return cuda_fail(e, "model set-up");
+  g->vmax = vmax;
+  if (g->d.nbl > 0) {
+    const double gmax = 3.0 * double(vmax) * log(1000.0) / (2.0 * g->d.nbl * g->d.h);
+    g->bscale = float(gmax * g->d.dt / 2.0 / (double(g->d.nbl) * g->d.nbl));
+  } else {
+    g->bscale = 0.0f;
+  }
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMemsetAsync(g->F.u[b], 0, g->ncell * 4, g->stream);
+    if (e) return cuda_fail(e, "wavefield reset");
+  }
+  g->F.cur = 0;
+  g->model_set = true;
+  e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "model set-up");
+  return FD_OK;
+}
+
+static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_points* src,
+                                const float* wavelet, const fd_points* rec, float* rec_out) {
+  if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
+  if (n0 < 0 || nsteps < 0) return fail(FD_ERR_ARG, "negative step range");
+  const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;
+  if ((nsrc && (!src->xyz || !wavelet)) || (nrec && (!rec->xyz || !rec_out)))
+    return fail(FD_ERR_ARG, "points given without their data array");
+  fd_status st = upload_tables(g, src, 1.0 / g->d.h, rec, g->tab);
+  if (st) return st;
+  const float* dval = nullptr;
+  float* drec = nullptr;
+  if ((st = stage_in(g, g->stage_val, nsrc ? wavelet : nullptr, size_t(n0 + nsteps) * nsrc,
+                     &dval)))
+    return st;
+  if ((st = stage_out(g, g->stage_rec, nrec ? rec_out : nullptr, size_t(nsteps) * nrec,
+                      &drec)))
+    return st;
+  RunSpec rs;
+  memset(&rs, 0, sizeof(rs));
+  rs.f = &g->F;
+  rs.allow_graph = 1;
+  rs.mode = kModeForward;
+  rs.nsteps = nsteps;
+  if (nsrc) {
+    rs.inj_start = static_cast<const int32_t*>(g->tab.inj_start.p);
+    rs.inj = static_cast<const InjEntry*>(g->tab.inj.p);
+    rs.inj_val = dval;
+    rs.inj_ncol = nsrc;
+    rs.inj_row0 = n0;
+    rs.inj_row_step = 1;
+  }
+  if (nrec) {
+    rs.rec_start = static_cast<const int32_t*>(g->tab.rec_start.p);
+    rs.recs = static_cast<const RecEntry*>(g->tab.recs.p);
+    rs.rec_out = drec;
+    rs.rec_ncol = nrec;
+    rs.rec_row0 = 0;
+    rs.rec_row_step = 1;
+  }
+  if ((st = run_steps(g, rs))) return st;
+  if ((st = check_device_error(g))) return st;
+  if (nrec) {
+    if ((st = check_finite(g, drec, size_t(nsteps) * nrec))) return st;
+    if ((st = finish_out(g, rec_out, drec, size_t(nsteps) * nrec))) return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "stream synchronize");
+  return FD_OK;
+}
+
+fd_status fd_propagate(fd_grid g, int32_t n0, int32_t nsteps, const fd_points* src,
+                       const float* wavelet, const fd_points* rec, float* rec_out) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  cudaSetDevice(g->d.device);
+  return propagate_impl(g, n0, nsteps, src, wavelet, rec, rec_out);
+}
+
+fd_status fd_forward(fd_grid g, const fd_points* src, const float* wavelet,
+                     const fd_points* rec, float* rec_out, float* u_out) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  cudaSetDevice(g->d.device);
+  if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
+  cudaError_t e;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMemsetAsync(g->F.u[b], 0, g->ncell * 4, g->stream);
+    if (e) return cuda_fail(e, "wavefield reset");
+  }
+  g->F.cur = 0;
+  fd_status st = propagate_impl(g, 0, g->d.nt, src, wavelet, rec, rec_out);
+  if (st) return st;
+  if (u_out) {
+    if ((st = copy_field(g, g->F.u[g->F.cur], u_out, FD_REGION_PHYSICAL, true))) return st;
+    e = cudaStreamSynchronize(g->stream);
+    if (e) return cuda_fail(e, "wavefield copy");
+  }
+  return FD_OK;
+}
+
+fd_status fd_set_wavefield(fd_grid g, const float* u_prev, const float* u_cur, int32_t region) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  if (region != FD_REGION_PHYSICAL && region != FD_REGION_PADDED)
+    return fail(FD_ERR_ARG, "bad region");
+  cudaSetDevice(g->d.device);
+  fd_status st;
+  if (u_prev &&
+      (st = copy_field(g, g->F.u[g->F.cur ^ 1], const_cast<float*>(u_prev), region, false)))
+    return st;
+  if (u_cur && (st = copy_field(g, g->F.u[g->F.cur], const_cast<float*>(u_cur), region, false)))
+    return st;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "wavefield copy");
+  return FD_OK;
+}
+
+fd_status fd_get_wavefield(fd_grid g, float* u_prev, float* u_cur, int32_t region) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  if (region != FD_REGION_PHYSICAL && region != FD_REGION_PADDED)
+    return fail(FD_ERR_ARG, "bad region");
+  cudaSetDevice(g->d.device);
+  fd_status st;
+  if (u_prev && (st = copy_field(g, g->F.u[g->F.cur ^ 1], u_prev, region, true))) return st;
+  if (u_cur && (st = copy_field(g, g->F.u[g->F.cur], u_cur, region, true))) return st;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "wavefield copy");
+  return FD_OK;
+}
+
+fd_status fd_get_info(fd_grid g, fd_grid_info* info) {
+  clear_error();
+  if (!g || !info) return fail(FD_ERR_ARG, "null argument");
+  info->nx_pad = g->Nx;
+  info->ny_pad = g->Ny;
+  info->nz_pad = g->Nz;
+  info->pitch = g->pitch;
+  info->tile_x = 4 * g->shape.tx;
+  info->tile_y = g->shape.ty;
+  info->zsplit = g->shape.zsplit;
+  info->v_max = g->vmax;
+  info->cfl_limit = g->cfl;
+  info->launches = g_launches.load();
+  info->step_ms = g->step_ms;
+  info->steps_timed = g->steps_timed;
+  return FD_OK;
+}
+
+static fd_status ensure_coef(fd_grid g) {
+  if (g->coef) return FD_OK;
+  cudaError_t e = dev_alloc(reinterpret_cast<void**>(&g->coef), size_t(g->R) * g->ncell * 4);
+  if (e) return cuda_fail(e, "coefficient allocation");
+  return build_maps(g);
+}
+
+fd_status fd_set_coefficients(fd_grid g, const float* c, int32_t mode) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  cudaSetDevice(g->d.device);
+  g->graph_valid = false;
+  if (mode == FD_COEF_TAYLOR) {
+    fd_weights(g->R, g->c);
+    g->percell = false;
+    return FD_OK;
+  }
+  if (!c) return fail(FD_ERR_ARG, "coefficients required");
+  if (mode == FD_COEF_UNIFORM) {
+    float h[kMaxR + 1];
+    cudaError_t e = cudaMemcpy(h, c, sizeof(float) * (g->R + 1), cudaMemcpyDefault);
+    if (e) return cuda_fail(e, "coefficient read");
+    for (int j = 0; j <= g->R; ++j) g->c[j] = h[j];
+    g->percell = false;
+    return FD_OK;
+  }
+  if (mode != FD_COEF_PER_CELL) return fail(FD_ERR_ARG, "bad coefficient mode");
+  if (g->R != 4) return fail(FD_ERR_ARG, "per-cell weights are compiled for space order 8");
+  fd_status st = ensure_coef(g);
+  if (st) return st;
+  const size_t np = size_t(g->d.nx) * g->d.ny * g->d.nz;
+  const float* dev = nullptr;
+  if ((st = stage_in(g, g->stage_aux, c, np * g->R, &dev))) return st;
+  cudaError_t e = pad_coefficients(dev, g->R, g->d.nx, g->d.ny, g->d.nz, g->d.nbl, g->Nx, g->Ny,
+                                   g->Nz, g->pitch, g->ncell, g->coef, g->stream);
+  if (!e) e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "coefficient set-up");
+  g->percell = true;
+  return FD_OK;
+}
+
+fd_status fd_set_learned_coefficients(fd_grid g, fd_mlp net, double f_hz) {
+  clear_error();
+  if (!g || !net) return fail(FD_ERR_ARG, "null argument");
+  if (g->R != 4) return fail(FD_ERR_ARG, "the network predicts space-order-8 weights");
+  if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
+  cudaSetDevice(g->d.device);
+  fd_status st = ensure_coef(g);
+  if (st) return st;
+  st = mlp_grid_coefficients(net, g->A, g->ncell, g->pitch, g->Nx, g->d.h, g->d.dt, f_hz,
+                             g->coef, g->stream);
+  if (st) return st;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "learned coefficients");
+  g->percell = true;
+  g->graph_valid = false;
+  return FD_OK;
+}
+
+fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t zsplit) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  if (zsplit < 1 || zsplit > g->Nz) return fail(FD_ERR_ARG, "zsplit must be in 1..nz_pad");
+  for (int i = 0; i < kNumShapes; ++i) {
+    if (4 * kShapes[i].tx == tile_x && kShapes[i].ty == tile_y) {
+      cudaSetDevice(g->d.device);
+      TileShape t = kShapes[i];
+      t.zsplit = zsplit;
+      set_shape(g, t);
+      return build_maps(g);
+    }
+  }
+  return fail(FD_ERR_ARG, "tile %dx%d is not compiled", tile_x, tile_y);
+}
+
+fd_status fd_set_debug(fd_grid g, int32_t key, int64_t value) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  switch (key) {
+    case FD_DEBUG_SKIP_PLANE:
+      g->debug_skip_plane = value < 0 ? -1 : int(value);
+      return FD_OK;
+    case FD_DEBUG_SPIN_LIMIT:
+      if (value <= 0) return fail(FD_ERR_ARG, "spin limit must be positive");
+      g->spin_limit = value;
+      return FD_OK;
+    case FD_DEBUG_NO_GRAPH:
+      g->no_graph = value != 0;
+      return FD_OK;
+  }
+  return fail(FD_ERR_ARG, "unknown debug key %d", key);
+}
+
+fd_status fd_set_profiling(fd_grid g, int32_t enabled) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  g->profiling = enabled != 0;
+  g->step_ms = 0.0;
+  g->steps_timed = 0;
+  return FD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Host-side state of a grid and the runtime helpers shared by the host
+// translation units (forward, adjoint, batch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/fd.h"
+#include "fd_internal.h"
+
+namespace fd {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes);
+  void release();
+};
+
+struct Tables {
+  DevBuf inj_start, inj, rec_start, recs;
+  int n_inj = 0, n_rec = 0;
+};
+
+// A pair of wavefield buffers with their tensor maps; u[cur] holds the
+// current field, u[cur^1] the previous one (overwritten by the next).
+struct Fields {
+  float* u[2] = {nullptr, nullptr};
+  CUtensorMap halo[2];
+  CUtensorMap tile[2];
+  int cur = 0;
+};
+
+// One run of consecutive steps.
+struct RunSpec {
+  Fields* f;
+  int allow_graph;
+  int mode;
+  int nsteps;
+  const int32_t* inj_start;
+  const InjEntry* inj;
+  const float* inj_val;
+  int inj_ncol, inj_row0, inj_row_step;
+  const int32_t* rec_start;
+  const RecEntry* recs;
+  float* rec_out;
+  int rec_ncol, rec_row0, rec_row_step;
+  float* e_base;      // kModeStoreE: e of step t at e_base + t*ncell
+  int e_idx0, e_idx_step;  // kModeAdjoint: e_in index of step t
+  float* grad;
+};
+
+struct GraphKey {
+  RunSpec spec;
+  int cur;
+  TileShape shape;
+  int skip;
+  float bscale;
+};
+
+constexpr int kNumShapes = 4;
+extern const TileShape kShapes[kNumShapes];
+
+}  // namespace fd
+
+struct fd_grid_s {
+  fd_grid_desc d;
+  int R = 1;
+  int Nx = 0, Ny = 0, Nz = 0;
+  int pitch = 0;
+  size_t ncell = 0;  // pitch * Ny * Nz
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  fd::Fields F;  // forward wavefields u^{n-1}, u^n
+  fd::Fields Z;  // adjoint wavefields (allocated on first use)
+  float* A = nullptr;
+  CUtensorMap mapA;
+  float* coef = nullptr;   // per-cell weights c_1..c_R, field j at coef + j*ncell
+  CUtensorMap mapC;
+  bool percell = false;
+  bool model_set = false;
+  double vmax = 0.0;
+  float bscale = 0.0f;
+  double c[fd::kMaxR + 1] = {};
+  double cfl = 0.0;
+  fd::TileShape shape = {};
+  int tiles_x = 0, tiles_y = 0, zlen = 0;
+  fd::Tables tab, tab_adj;
+  fd::DevBuf stage_val, stage_rec, stage_aux, recbuf;
+  fd::DevBuf ckpt, ebuf, gpad, resid;
+  int32_t* d_err = nullptr;  // [0] wait-timeout word, [1] finite count, [4..6] scratch
+  long long spin_limit = 0;
+  int debug_skip_plane = -1;
+  bool no_graph = false;
+  bool profiling = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double step_ms = 0.0;
+  long long steps_timed = 0;
+  bool graph_valid = false;
+  cudaGraphExec_t gexec = nullptr;
+  fd::GraphKey gkey = {};
+};
+
+namespace fd {
+
+fd_status fail(fd_status st, const char* fmt, ...);
+fd_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+cudaError_t dev_alloc(void** p, size_t bytes);
+bool is_device_ptr(const void* p);
+fd_status build_maps(fd_grid g);
+fd_status build_field_maps(fd_grid g, Fields& f);
+void set_shape(fd_grid g, TileShape t);
+TileShape default_shape(int R, int Nx, int Ny, int Nz);
+size_t step_smem(int R, const TileShape& t);
+cudaError_t launch_step(int R, const TileShape& t, int mode, const CUtensorMap& h,
+                        const CUtensorMap& p, const CUtensorMap& A, const CUtensorMap& C,
+                        const StepArgs& a, cudaStream_t s);
+StepArgs base_args(fd_grid g);
+fd_status upload_tables(fd_grid g, const fd_points* src, double src_scale,
+                        const fd_points* rec, Tables& t);
+fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
+                          std::vector<int32_t>& start, std::vector<InjEntry>& out);
+fd_status build_receivers(fd_grid g, const fd_points* pts, std::vector<int32_t>& start,
+                          std::vector<RecEntry>& out);
+fd_status stage_in(fd_grid g, DevBuf& buf, const float* p, size_t n, const float** out);
+fd_status stage_out(fd_grid g, DevBuf& buf, float* p, size_t n, float** out);
+fd_status finish_out(fd_grid g, float* host, const float* dev, size_t n);
+fd_status run_steps(fd_grid g, const RunSpec& rs);
+fd_status check_device_error(fd_grid g);
+fd_status check_finite(fd_grid g, const float* dev, size_t n);
+fd_status copy_field(fd_grid g, float* dev_field, void* user, int region, bool to_user);
+
+}  // namespace fd

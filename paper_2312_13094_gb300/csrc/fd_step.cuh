@@ -1,0 +1,442 @@
+// Damped leapfrog step of the acoustic wave equation for sm_103a.
+//
+// Eq. 1 (App. A) discretised as in Sec. IV-B: one launch advances
+//   (1+b) u^{n+1} = 2u^n - (1-b) u^{n-1} + A (lap(u^n) + s^n),
+// A = dt^2 / (m h^2) (stored per cell), lap = sum_axes sum_j c_|j| u(i+j e_a)
+// with the zero ghost of Sec. III beyond the padded grid, b from the sponge
+// depth, s^n the trilinear source term, and rec[n] = I(u^n) (Sec. III
+// "Sparse data") read from the same staged planes.
+//
+// Design (2.5D streaming, Blackwell-native):
+//  * A CTA owns an xy tile of BX x BY points (4 consecutive x per thread,
+//    one row per thread) and sweeps a range of z planes.
+//  * Each plane of u^n, with an R-row and RX-column halo (RX = R rounded up
+//    to 4 floats so that the TMA x coordinate stays 16-byte aligned), is
+//    brought into shared memory by one 3D TMA tile load into a ring of
+//    SU = R + 1 + PF slots, each completed on its own mbarrier.  Loads that
+//    fall outside the grid are zero-filled by the TMA unit, which is exactly
+//    the read-only zero halo, so no ghost cells are stored in HBM.
+//  * u^{n-1} and A tiles come through a second TMA ring of PF + 1 slots.
+//  * z neighbours live in a per-thread register queue of 2R+1 float4s; x and
+//    y neighbours are read from the staged plane with 128-bit loads.
+//  * Source injection and receiver interpolation use per-tile entry lists
+//    sorted by z, so a tile without points pays one compare per plane.
+//  * Every mbarrier wait is bounded (clock64); on expiry the CTA records an
+//    error, waits (bounded) for its own copies still in flight, and returns.
+#pragma once
+
+#include "fd_internal.h"
+
+namespace fd {
+
+template <int R, int TX, int TY, int PF, int NC = 0>
+struct Cfg {
+  static constexpr int RX = ((R + 3) / 4) * 4;
+  static constexpr int BX = 4 * TX;
+  static constexpr int BY = TY;
+  static constexpr int NT = TX * TY;
+  static constexpr int W = BX + 2 * RX;
+  static constexpr int H = BY + 2 * R;
+  static constexpr int SU = R + 1 + PF;
+  static constexpr int SA = PF + 1;
+  static constexpr uint32_t UBYTES = W * H * 4;
+  static constexpr uint32_t UPITCH = (UBYTES + 127) / 128 * 128;
+  static constexpr uint32_t TBYTES = BX * BY * 4;
+  static constexpr uint32_t TPITCH = (TBYTES + 127) / 128 * 128;
+  static constexpr uint32_t OFF_P = SU * UPITCH;
+  static constexpr uint32_t OFF_A = OFF_P + SA * TPITCH;
+  static constexpr uint32_t OFF_C = OFF_A + SA * TPITCH;      // NC coefficient tiles
+  static constexpr uint32_t OFF_BAR = OFF_C + SA * NC * TPITCH;
+  static constexpr uint32_t SMEM = OFF_BAR + (SU + SA) * 8 + 128;
+  static constexpr int NROW4 = 2 * RX / 4 + 1;
+  static_assert(W <= 256 && H <= 256, "TMA box too large");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map,
+                                            int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ int sponge_depth(int g, int nbl, int n) {
+  int d = nbl - g;
+  int e = g - (n + nbl - 1);
+  d = d > e ? d : e;
+  return d > 0 ? d : 0;
+}
+
+__device__ __forceinline__ float lane(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// One CTA: the xy tile (tile_x, tile_y), z chunk zc.  All threads of the CTA
+// must call this with the same arguments.
+template <int R, int TX, int TY, int PF, int MODE>
+__device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
+                                           const CUtensorMap* tm_prev,
+                                           const CUtensorMap* tm_A,
+                                           const CUtensorMap* tm_C,
+                                           const StepArgs& a, float* __restrict__ out,
+                                           int tile_x, int tile_y, int zc,
+                                           unsigned char* smem) {
+  constexpr int NC = (MODE == kModePerCell) ? R : 0;
+  using C = Cfg<R, TX, TY, PF, NC>;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX;
+  const int ty = tid / TX;
+  const int x0 = tile_x * C::BX;
+  const int y0 = tile_y * C::BY;
+  const int zbeg = zc * a.zlen;
+  const int zend = min(a.Nz, zbeg + a.zlen);
+  if (zbeg >= zend) return;
+  const int zl = zend - zbeg;
+  const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
+  const long long limit = a.spin_limit;
+
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar_u0 = sbase + C::OFF_BAR;
+  const uint32_t bar_a0 = bar_u0 + 8 * C::SU;
+  const float* ubuf = reinterpret_cast<const float*>(smem);
+  const float* pbuf = reinterpret_cast<const float*>(smem + C::OFF_P);
+  const float* abuf = reinterpret_cast<const float*>(smem + C::OFF_A);
+  const float* cbuf = reinterpret_cast<const float*>(smem + C::OFF_C);
+
+  if (tid == 0) {
+    for (int s = 0; s < C::SU; ++s) mbar_init(bar_u0 + 8 * s, 1);
+    for (int s = 0; s < C::SA; ++s) mbar_init(bar_a0 + 8 * s, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // producer state (meaningful in thread 0 only)
+  int ju_next = 0, ia_next = 0;
+  auto issue_u = [&](int j) {
+    if (j >= J) return;
+    ju_next = j + 1;
+    const int z = zbeg - R + j;
+    if (z == a.debug_skip_plane) return;
+    const int slot = j % C::SU;
+    const uint32_t bar = bar_u0 + 8 * slot;
+    mbar_expect_tx(bar, C::UBYTES);
+    tma_load_3d(sbase + slot * C::UPITCH, tm_halo, x0 - C::RX, y0 - R, z, bar);
+  };
+  auto issue_a = [&](int i) {
+    if (i >= zl) return;
+    ia_next = i + 1;
+    const int z = zbeg + i;
+    const int slot = i % C::SA;
+    const uint32_t bar = bar_a0 + 8 * slot;
+    mbar_expect_tx(bar, (2 + NC) * C::TBYTES);
+    tma_load_3d(sbase + C::OFF_P + slot * C::TPITCH, tm_prev, x0, y0, z, bar);
+    tma_load_3d(sbase + C::OFF_A + slot * C::TPITCH, tm_A, x0, y0, z, bar);
+#pragma unroll
+    for (int j = 0; j < NC; ++j)  // coefficient field j sits j*Nz planes further
+      tma_load_3d(sbase + C::OFF_C + (slot * NC + j) * C::TPITCH, tm_C, x0, y0,
+                  z + j * a.Nz, bar);
+  };
+
+  if (tid == 0) {
+    for (int j = 0; j < C::SU; ++j) issue_u(j);
+    for (int i = 0; i < C::SA; ++i) issue_a(i);
+  }
+
+  const int crow = (ty + R) * C::W + 4 * tx + C::RX;  // centre float offset
+  float4 q[2 * R + 1];
+  bool bad = false;
+
+#pragma unroll
+  for (int j = 0; j < 2 * R; ++j) {
+    const int slot = j % C::SU;
+    bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, limit);
+    q[j] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
+    if (j < R) {
+      if (__syncthreads_or(bad)) goto fail;
+      if (tid == 0) issue_u(j + C::SU);
+    }
+  }
+
+  {
+    // entry ranges of this tile, skipping entries below this z chunk
+    const int tile = tile_y * a.tiles_x + tile_x;
+    int ip = 0, iend = 0, rp = 0, rend = 0;
+    if (a.inj_start) {
+      ip = a.inj_start[tile];
+      iend = a.inj_start[tile + 1];
+      while (ip < iend && a.inj[ip].z < zbeg) ++ip;
+    }
+    if (a.rec_start) {
+      rp = a.rec_start[tile];
+      rend = a.rec_start[tile + 1];
+      while (rp < rend && a.recs[rp].z < zbeg) ++rp;
+    }
+
+    const int gy = y0 + ty;
+    const int gx = x0 + 4 * tx;
+    const bool row_ok = gy < a.Ny;
+    const bool col_ok = gx < a.Nx;
+    const int dyv = sponge_depth(gy, a.nbl, a.ny);
+    float dxx[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int d = sponge_depth(gx + l, a.nbl, a.nx);
+      dxx[l] = static_cast<float>(d * d + dyv * dyv);
+    }
+    const float c0x3 = 3.0f * a.c[0];
+
+    for (int k = zbeg; k < zend; ++k) {
+      const int jk = k - zbeg + R;
+      const int ik = k - zbeg;
+      const int jn = jk + R;
+      {
+        const int slot = jn % C::SU;
+        bad |= !mbar_wait(bar_u0 + 8 * slot, (jn / C::SU) & 1, limit);
+        q[2 * R] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
+      }
+      const int aslot = ik % C::SA;
+      bad |= !mbar_wait(bar_a0 + 8 * aslot, (ik / C::SA) & 1, limit);
+
+      const float* P = ubuf + (jk % C::SU) * (C::UPITCH / 4);
+      float xr[4 * C::NROW4];
+#pragma unroll
+      for (int m = 0; m < C::NROW4; ++m) {
+        const float4 v = *reinterpret_cast<const float4*>(P + (ty + R) * C::W + 4 * tx + 4 * m);
+        xr[4 * m + 0] = v.x;
+        xr[4 * m + 1] = v.y;
+        xr[4 * m + 2] = v.z;
+        xr[4 * m + 3] = v.w;
+      }
+      const int aslot_c = ik % C::SA;
+      float lap[4];
+      if (MODE == kModePerCell) {
+        // per-cell weights c_1..c_R from the staged coefficient tiles,
+        // c_0 = -2 sum_j c_j
+        float cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int jj = 1; jj <= R; ++jj) {
+          const float4 cv = *reinterpret_cast<const float4*>(
+              cbuf + (aslot_c * NC + (jj - 1)) * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+          const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
+          const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
+            const float sy = lane(ym, l) + lane(yp, l);
+            const float sz = lane(q[R - jj], l) + lane(q[R + jj], l);
+            const float cj = lane(cv, l);
+            cs[l] += cj;
+            lap[l] = (jj == 1) ? cj * ((sx + sy) + sz) : fmaf(cj, (sx + sy) + sz, lap[l]);
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) lap[l] = fmaf(-6.0f * cs[l], xr[C::RX + l], lap[l]);
+      } else {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) lap[l] = c0x3 * xr[C::RX + l];
+#pragma unroll
+        for (int jj = 1; jj <= R; ++jj) {
+          const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
+          const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
+          const float cj = a.c[jj];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
+            const float sy = lane(ym, l) + lane(yp, l);
+            const float sz = lane(q[R - jj], l) + lane(q[R + jj], l);
+            lap[l] = fmaf(cj, (sx + sy) + sz, lap[l]);
+          }
+        }
+      }
+
+      // point sources of this plane (owner thread adds its share)
+      float src[4] = {0.f, 0.f, 0.f, 0.f};
+      while (ip < iend) {
+        const InjEntry e = a.inj[ip];
+        if (e.z != k) break;
+        if (e.ly == ty && (e.lx >> 2) == tx) {
+          const float val = e.w * a.inj_val[static_cast<size_t>(a.inj_row) * a.inj_ncol + e.col];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) src[l] += ((e.lx & 3) == l) ? val : 0.f;
+        }
+        ++ip;
+      }
+
+      const float4 up = *reinterpret_cast<const float4*>(pbuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+      const float4 Av = *reinterpret_cast<const float4*>(abuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+      const int dz = sponge_depth(k, a.nbl, a.nz);
+      const float dzz = static_cast<float>(dz * dz);
+      float res[4], ev[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float b = a.bscale * (dxx[l] + dzz);
+        const float uc = lane(q[R], l);
+        const float e = lane(Av, l) * (lap[l] + src[l]);
+        float t = fmaf(-(1.0f - b), lane(up, l), 2.0f * uc) + e;
+        if (b != 0.0f) t = t / (1.0f + b);
+        res[l] = (gx + l < a.Nx) ? t : 0.0f;
+        ev[l] = (gx + l < a.Nx) ? e : 0.0f;
+      }
+      if (row_ok && col_ok) {
+        const size_t off = (static_cast<size_t>(k) * a.Ny + gy) * a.pitch + gx;
+        *reinterpret_cast<float4*>(out + off) = make_float4(res[0], res[1], res[2], res[3]);
+        if (MODE == kModeStoreE)
+          *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+        if (MODE == kModeAdjoint) {
+          const float4 ein = *reinterpret_cast<const float4*>(a.e_in + off);
+          float4 g = *reinterpret_cast<float4*>(a.grad + off);
+          g.x -= q[R].x * ein.x * a.inv_dt2;
+          g.y -= q[R].y * ein.y * a.inv_dt2;
+          g.z -= q[R].z * ein.z * a.inv_dt2;
+          g.w -= q[R].w * ein.w * a.inv_dt2;
+          *reinterpret_cast<float4*>(a.grad + off) = g;
+        }
+      }
+
+      // receivers whose floor node lies in this plane: one thread each,
+      // trilinear over planes k and k+1 (both staged)
+      {
+        int rq = rp;
+        while (rq < rend && a.recs[rq].z == k) ++rq;
+        const float* P1 = ubuf + ((jk + 1) % C::SU) * (C::UPITCH / 4);
+        for (int e = rp + tid; e < rq; e += C::NT) {
+          const RecEntry r = a.recs[e];
+          const int o = (r.ly + R) * C::W + r.lx + C::RX;
+          const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
+          const float p0 = gy0 * (gx0 * P[o] + r.fx * P[o + 1]) +
+                           r.fy * (gx0 * P[o + C::W] + r.fx * P[o + C::W + 1]);
+          const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
+                           r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
+          a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
+              (1.0f - r.fz) * p0 + r.fz * p1;
+        }
+        rp = rq;
+      }
+
+      if (__syncthreads_or(bad)) goto fail;
+      if (tid == 0) {
+        issue_u(jk + C::SU);
+        issue_a(ik + C::SA);
+      }
+#pragma unroll
+      for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+    }
+  }
+  // every issued copy has been waited for; release the barriers so the
+  // shared memory can host the next column
+  if (tid == 0) {
+    for (int s = 0; s < C::SU; ++s) mbar_inval(bar_u0 + 8 * s);
+    for (int s = 0; s < C::SA; ++s) mbar_inval(bar_a0 + 8 * s);
+  }
+  __syncthreads();
+  return;
+
+fail:
+  if (tid == 0) {
+    atomicOr(a.err, 1);
+    // wait (bounded) for every copy this CTA still has in flight
+    for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
+      if (zbeg - R + j == a.debug_skip_plane) continue;
+      mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, limit);
+    }
+    for (int i = max(0, ia_next - C::SA); i < ia_next; ++i)
+      mbar_wait(bar_a0 + 8 * (i % C::SA), (i / C::SA) & 1, limit);
+  }
+}
+
+template <int R, int TX, int TY, int PF, int MODE>
+__global__ void __launch_bounds__(TX* TY, 2)
+    step_kernel(const __grid_constant__ CUtensorMap halo,
+                const __grid_constant__ CUtensorMap tprev,
+                const __grid_constant__ CUtensorMap tA,
+                const __grid_constant__ CUtensorMap tC,
+                const __grid_constant__ StepArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  run_column<R, TX, TY, PF, MODE>(&halo, &tprev, &tA, &tC, a, a.out, blockIdx.x,
+                                  blockIdx.y, blockIdx.z, smem);
+}
+
+// Many shots in one persistent launch: CTAs pull {shot, tile, z chunk} items
+// (sorted longest first) from an atomic counter; each item is one column of
+// run_column on that shot's buffers.  Time step t selects the buffer parity
+// and the wavelet / receiver rows.
+template <int R, int TX, int TY, int PF>
+__global__ void __launch_bounds__(TX* TY, 2)
+    batch_kernel(const BatchShot* __restrict__ shots, const int4* __restrict__ work,
+                 int nwork, int* __restrict__ counter, int t) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  __shared__ StepArgs sa;
+  __shared__ int item;
+  const int cur = t & 1;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = item;
+    if (it >= nwork) break;
+    const int4 w = work[it];
+    const BatchShot* S = shots + w.x;
+    if (threadIdx.x == 0) {
+      sa = S->args;
+      sa.inj_row = t;
+      sa.rec_row = t;
+    }
+    __syncthreads();
+    run_column<R, TX, TY, PF, kModeForward>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->A, sa,
+                                            S->u[cur ^ 1], w.y, w.z, w.w, smem);
+    __syncthreads();
+  }
+}
+
+}  // namespace fd

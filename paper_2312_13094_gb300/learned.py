@@ -1,0 +1,205 @@
+"""Learned per-cell stencil weights: training data from fine-grid runs, GPU
+training with the library's own kernels, and the coarse-vs-fine evaluation.
+
+Every numerical step runs in libfd.so (fine and coarse propagation, stencil
+sampling, sample assembly, network training and inference); this module only
+schedules the calls and moves arrays.
+
+Setting (coarse solve = every second fine node, twice the time step):
+  fine    n^3 + nbl_f layer, h_f, space order 16, dt_f, nt_f steps
+  coarse  (n/2)^3 + nbl_f/2, h_c = 2 h_f, space order 8 (plain or learned),
+          dt_c = 2 dt_f, nt_c = nt_f / 2 steps; coarse rec[k] vs fine rec[2k].
+Velocity models: 3-8 horizontal layers, v in [1.5, 4.5] km/s, interfaces
+smoothed over 40 m, drawn with seeded splitmix64 streams.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import binding as fd
+from . import workloads as wl
+
+
+def pair(seed: int, n: int = 512, h: float = 10.0, dt: float = 0.8, nt: int = 1250,
+         nbl: int = 40, f_hz: float = 12.0, nrec: int = 256):
+    """Fine and coarse workloads on the same seeded layered model."""
+    assert n % 2 == 0 and nt % 2 == 0 and nbl % 2 == 0
+    nf = (n, n, n)
+    v = wl.layered_model(nf, h, seed)
+    ext = (n - 1) * h
+    # source at the centre in x/y, 10 fine cells deep; receivers on a line
+    src = np.array([[n // 2 * h, n // 2 * h, 10 * h]])
+    xs = np.arange(nrec) * 2 * h * max(1, (n // 2 - 1) // max(nrec - 1, 1))
+    xs = xs[xs <= ext]
+    rec = np.stack([xs, np.full(len(xs), n // 2 * h), np.full(len(xs), 4 * h)], 1)
+    wav_f = wl.ricker(nt, dt, f_hz).reshape(nt, 1)
+    fine = dict(name=f"fine {n}^3 h{h:g} SO16", n=nf, h=h, space_order=16, nbl=nbl, dt=dt,
+                nt=nt, v=v, src=src, rec=rec, wavelet=wav_f, f0=f_hz)
+    vc = np.ascontiguousarray(v[::2, ::2, ::2])
+    wav_c = wl.ricker(nt // 2, 2 * dt, f_hz).reshape(nt // 2, 1)
+    coarse = dict(name=f"coarse {n // 2}^3 h{2 * h:g} SO8", n=(n // 2,) * 3, h=2 * h,
+                  space_order=8, nbl=nbl // 2, dt=2 * dt, nt=nt // 2, v=vc, src=src,
+                  rec=rec, wavelet=wav_c, f0=f_hz)
+    return fine, coarse
+
+
+def run_forward(w, device=0, net=None, space_order=None, timed=False):
+    """Receivers of one forward run (and its device time in ms if timed)."""
+    import torch
+    so = w["space_order"] if space_order is None else space_order
+    ww = dict(w, space_order=so)
+    with fd.Grid.from_workload(ww, device=device) as g:
+        g.set_model(w["v"])
+        if net is not None:
+            fd.check(fd.fd_set_learned_coefficients(g.handle, net, float(w["f0"])),
+                     "fd_set_learned_coefficients")
+        rec = torch.zeros((w["nt"], len(w["rec"])), device=f"cuda:{device}")
+        wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).to(f"cuda:{device}")
+        ms = None
+        if timed:
+            fd.check(g.forward(w["src"], wav, w["rec"], rec), "warm-up")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        fd.check(g.forward(w["src"], wav, w["rec"], rec), "fd_forward")
+        torch.cuda.synchronize()
+        if timed:
+            ms = (time.perf_counter() - t0) * 1e3
+        return rec.cpu().numpy(), ms
+
+
+def training_samples(fine, coarse, ncell: int = 16384, ntimes: int = 8, seed: int = 0,
+                     min_src_dist: int = 5, device: int = 0):
+    """Samples (device tensor [m, 10]) from one fine run: at `ntimes` coarse
+    times in the second half of the run, `ncell` random coarse cells (at
+    least `min_src_dist` coarse cells from the source), stencils taken at
+    fine steps 2k-2, 2k, 2k+2 with stride 2."""
+    import torch
+    dev = f"cuda:{device}"
+    nc = coarse["n"]
+    nbl_f = fine["nbl"]
+    rng = np.random.default_rng(seed)
+    ntc = coarse["nt"]
+    times = np.sort(rng.choice(np.arange(ntc // 2, ntc - 1), ntimes, replace=False))
+    src_c = np.round(np.asarray(coarse["src"][0]) / coarse["h"]).astype(int)
+    cells_c = []
+    while len(cells_c) < ncell:
+        c = rng.integers(0, nc[0], size=(ncell, 3))
+        d = np.abs(c - src_c[None, :]).max(axis=1)
+        cells_c.extend(c[d >= min_src_dist].tolist())
+    cells_c = np.array(cells_c[:ncell], dtype=np.int32)        # (x, y, z) coarse
+    cells_f = np.ascontiguousarray(2 * cells_c + nbl_f, dtype=np.int32)  # padded fine
+    vel = torch.from_numpy(np.ascontiguousarray(
+        fine["v"][2 * cells_c[:, 2], 2 * cells_c[:, 1], 2 * cells_c[:, 0]],
+        dtype=np.float32)).to(dev)
+    width = 1 + 6 * 4
+    out = []
+    with fd.Grid.from_workload(fine, device=device) as g:
+        g.set_model(fine["v"])
+        wav = torch.from_numpy(np.ascontiguousarray(fine["wavelet"])).to(dev)
+        step = 0
+        for tk in times:
+            snaps = []
+            for fstep in (2 * tk - 2, 2 * tk, 2 * tk + 2):
+                if fstep > step:
+                    fd.check(g.propagate(step, fstep - step, fine["src"], wav), "fd_propagate")
+                    step = fstep
+                buf = torch.zeros((ncell, width), device=dev)
+                fd.check(fd.fd_sample_stencil(g.handle, ncell, cells_f.ctypes.data, 2, 4,
+                                              buf.data_ptr()), "fd_sample_stencil")
+                snaps.append(buf)
+            ms = float((snaps[1] ** 2).mean())
+            s = torch.zeros((ncell, fd.FD_MLP_SAMPLE), device=dev)
+            fd.check(fd.fd_mlp_make_samples(ncell, snaps[0].data_ptr(), snaps[1].data_ptr(),
+                                            snaps[2].data_ptr(), vel.data_ptr(),
+                                            coarse["h"], coarse["dt"], coarse["f0"],
+                                            1e-3 * ms + 1e-30, s.data_ptr()),
+                     "fd_mlp_make_samples")
+            out.append(s)
+    return torch.cat(out)
+
+
+class Network:
+    """Owns an fd_mlp handle."""
+
+    def __init__(self, params=None, device=0):
+        import ctypes
+        h = ctypes.c_void_p()
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        fd.check(fd.fd_mlp_create(device, None if p is None else p.ctypes.data,
+                                  ctypes.byref(h)), "fd_mlp_create")
+        self.handle = h
+
+    def params(self):
+        out = np.zeros(fd.FD_MLP_NPARAM, np.float32)
+        fd.check(fd.fd_mlp_get_params(self.handle, out.ctypes.data), "fd_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        fd.check(fd.fd_mlp_set_params(self.handle, p.ctypes.data), "fd_mlp_set_params")
+
+    def loss_grad(self, samples):
+        import ctypes
+        loss = ctypes.c_double()
+        g = np.zeros(fd.FD_MLP_NPARAM, np.float32)
+        fd.check(fd.fd_mlp_loss_grad(self.handle, samples.shape[0], fd._ptr(samples),
+                                     ctypes.byref(loss), g.ctypes.data), "fd_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, samples, epochs, batch, lr):
+        import ctypes
+        loss = ctypes.c_double()
+        fd.check(fd.fd_mlp_train(self.handle, samples.shape[0], fd._ptr(samples), epochs,
+                                 batch, lr, ctypes.byref(loss)), "fd_mlp_train")
+        return loss.value
+
+    def coefficients(self, features):
+        features = np.ascontiguousarray(features, np.float32)
+        out = np.zeros((features.shape[0], 4), np.float32)
+        fd.check(fd.fd_mlp_coefficients(self.handle, features.shape[0], features.ctypes.data,
+                                        out.ctypes.data), "fd_mlp_coefficients")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fd.fd_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def init_params(seed: int, scale_out: float = 0.1):
+    """Seeded initial parameters (hidden layers He-scaled, output layer scaled
+    by `scale_out`), drawn from splitmix64 normals."""
+    H, NIN, NOUT = 64, 4, 8
+    z = wl.normal(seed, H * NIN + H * H + NOUT * H)
+    W1 = z[:H * NIN] * np.sqrt(2.0 / NIN)
+    W2 = z[H * NIN:H * NIN + H * H] * np.sqrt(2.0 / H)
+    W3 = z[H * NIN + H * H:] * np.sqrt(1.0 / H) * scale_out
+    return np.concatenate([W1, np.zeros(H), W2, np.zeros(H), W3, np.zeros(NOUT)]).astype(
+        np.float32)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True):
+    """Per held-out model: receiver rel. L2 of coarse plain and coarse learned
+    against the fine SO 16 solve (fine rec[2k]), and the GPU times."""
+    rows = []
+    for s in seeds:
+        fine, coarse = pair(s, n=n, nt=nt)
+        rf, tf = run_forward(fine, device, timed=timed)
+        ref = rf[::2]
+        rp, tp = run_forward(coarse, device, timed=timed)
+        rl, tlr = run_forward(coarse, device, net=net.handle, timed=timed)
+        rows.append(dict(seed=s, plain=rel_l2(rp, ref), learned=rel_l2(rl, ref),
+                         ms_fine=tf, ms_plain=tp, ms_learned=tlr))
+    return rows

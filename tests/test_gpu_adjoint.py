@@ -1,0 +1,122 @@
+"""GPU adjoint gradient (checkpointed, through the C ABI) against the FP64
+oracle gradient and against central differences of the GPU forward model.
+
+Gradient tolerance: relative L2 <= 1e-4.  The gradient is a sum over all
+time steps of products of two FP32 fields (adjoint and e = dt^2/m (L u + s)),
+each carrying ~1e-6 relative error after the forward and backward sweeps, so
+the sum is held to 1e-4 rather than the wavefield's 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_13094_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2312_13094_gb300 import build
+    build.build()
+    from paper_2312_13094_gb300 import binding
+    return binding
+
+
+def problem(so=8, n=(26, 22, 20), nbl=5, nt=70):
+    w = wl.adjoint_256(n=n[0], nt=nt, nbl=nbl)
+    h = w["h"]
+    v = wl.layered_model(n, h, 17, vmin=1.8, vmax=2.6)
+    rng = np.random.default_rng(4)
+    v = (v * (1 + 0.03 * rng.uniform(-1, 1, v.shape))).astype(np.float32)
+    ext = [(d - 1) * h for d in n]
+    src = np.array([[0.5 * ext[0], 0.45 * ext[1], 0.3 * ext[2]]])
+    rec = np.array([[x, y, 0.8 * ext[2]] for x in np.linspace(0, ext[0], 5)
+                    for y in np.linspace(0.1 * ext[1], 0.9 * ext[1], 4)])
+    dt = 0.35 * h / float(v.max())
+    wav = wl.ricker(nt, dt, 30.0).reshape(nt, 1)
+    w.update(n=n, space_order=so, v=v, src=src, rec=rec, dt=dt, wavelet=wav, nt=nt)
+    return w
+
+
+def og_of(w):
+    return oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=w["space_order"] // 2, nbl=w["nbl"])
+
+
+def gpu_grad(fd, w, d_obs, nc, v=None):
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"] if v is None else v)
+        grad = np.zeros(g.phys_shape, np.float32)
+        st, loss = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], d_obs, nc, grad)
+        fd.check(st, "fd_adjoint_gradient")
+        return grad, loss
+
+
+def observed(w, scale=1.03):
+    m_true = 1.0 / (w["v"].astype(np.float64) * scale) ** 2
+    return oracle.forward(og_of(w), m_true, w["nt"], w["src"], w["wavelet"],
+                          w["rec"])["rec"].astype(np.float32)
+
+
+@pytest.mark.parametrize("so", [4, 8, 16])
+def test_gradient_matches_oracle(fd, so):
+    w = problem(so)
+    d_obs = observed(w)
+    grad, loss = gpu_grad(fd, w, d_obs, 7)
+    m = 1.0 / w["v"].astype(np.float64) ** 2
+    ref, rloss, _ = oracle.adjoint_gradient(og_of(w), m, w["nt"], w["src"], w["wavelet"],
+                                            w["rec"], d_obs=d_obs.astype(np.float64))
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    err = np.linalg.norm(grad - ref) / np.linalg.norm(ref)
+    assert err <= 1e-4, err
+
+
+def test_checkpoint_count_does_not_change_the_result(fd):
+    w = problem(8, nt=45)
+    d_obs = observed(w)
+    ref, _ = gpu_grad(fd, w, d_obs, 1)
+    for nc in (2, 5, 45, 1000):
+        g, _ = gpu_grad(fd, w, d_obs, nc)
+        np.testing.assert_array_equal(g, ref)
+
+
+def test_backward_is_the_vector_jacobian_product(fd):
+    w = problem(8, nt=40)
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal((w["nt"], len(w["rec"]))).astype(np.float32)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        grad = np.zeros(g.phys_shape, np.float32)
+        fd.check(g.backward(w["src"], w["wavelet"], w["rec"], r, 4, grad), "fd_backward")
+    m = 1.0 / w["v"].astype(np.float64) ** 2
+    ref, _, _ = oracle.adjoint_gradient(og_of(w), m, w["nt"], w["src"], w["wavelet"],
+                                        w["rec"], residual=r.astype(np.float64))
+    assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_directional_derivative_by_central_differences_on_gpu(fd):
+    """<g, dm> against (J(m + e dm) - J(m - e dm)) / 2e, e = 1e-3, both from the
+    GPU path (the anomaly shape is the perturbation direction)."""
+    w = problem(8, nt=60)
+    d_obs = observed(w)
+    m = (1.0 / w["v"].astype(np.float64) ** 2)
+    zz, yy, xx = np.meshgrid(*(np.arange(s) for s in m.shape), indexing="ij")
+    c = [s / 2 for s in m.shape]
+    phi = np.exp(-((zz - c[0]) ** 2 + (yy - c[1]) ** 2 + (xx - c[2]) ** 2) / (2 * 3.0 ** 2))
+    eps = 1e-3
+    grad, _ = gpu_grad(fd, w, d_obs, 5)
+    dm = m * phi
+    losses = []
+    for sgn in (1, -1):
+        mm = (m + sgn * eps * dm).astype(np.float32)
+        with fd.Grid.from_workload(w) as g:
+            g.set_model(mm, fd.FD_MODEL_M)
+            rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+            fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec), "fd_forward")
+        losses.append(0.5 * np.sum((rec.astype(np.float64) - d_obs) ** 2))
+    fd_dir = (losses[0] - losses[1]) / (2 * eps)
+    ad_dir = float(np.sum(grad.astype(np.float64) * dm))
+    assert abs(fd_dir - ad_dir) <= 2e-2 * abs(ad_dir), (fd_dir, ad_dir)

@@ -1,0 +1,238 @@
+"""GPU parity of the forward path (libfd.so through the C ABI) against the
+FP64 oracle on the same seeded inputs.
+
+Tolerance: relative L2 <= 1e-5 on wavefields and receivers (FP32 GPU vs FP64
+oracle), as the method's target states; single steps are compared element
+by element.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_13094_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2312_13094_gb300 import build
+    build.build()
+    from paper_2312_13094_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def oracle_grid(w):
+    return oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=w["space_order"] // 2, nbl=w["nbl"])
+
+
+def run_gpu(fd, w, tile=None, zsplit=1, nt=None):
+    nt = w["nt"] if nt is None else nt
+    with fd.Grid.from_workload(w, nt=nt) as g:
+        if tile is not None:
+            g.set_tile(tile[0], tile[1], zsplit)
+        g.set_model(w["v"])
+        rec = np.zeros((nt, len(w["rec"])), np.float32)
+        u = np.zeros(g.phys_shape, np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec, u), "fd_forward")
+        return rec, u
+
+
+def run_oracle(w, nt=None):
+    nt = w["nt"] if nt is None else nt
+    out = oracle.forward(oracle_grid(w), 1.0 / w["v"].astype(np.float64) ** 2, nt,
+                         w["src"], w["wavelet"], w["rec"])
+    nb = w["nbl"]
+    u = out["u_cur"]
+    if nb:
+        u = u[nb:-nb, nb:-nb, nb:-nb]
+    return out["rec"], u
+
+
+def ragged_workload(so, n=(37, 29, 23), nbl=5, nt=40, seed=5):
+    h = 10.0
+    v = wl.layered_model(n, h, seed, vmin=1.5, vmax=3.0)
+    rng = np.random.default_rng(seed)
+    v = (v * (1.0 + 0.05 * rng.uniform(-1, 1, v.shape))).astype(np.float32)
+    dt = 0.35 * h / float(v.max())
+    ext = [(d - 1) * h for d in n]
+    src = np.array([[0.37 * ext[0], 0.61 * ext[1], 0.45 * ext[2]],
+                    [0.0, ext[1], 0.2 * ext[2]]])
+    rec = np.array([[0.0, 0.0, 0.0], [ext[0], ext[1], ext[2]], [ext[0], 0.5 * h, 1.5 * h]]
+                   + [[x, 0.33 * ext[1], 2.5 * h] for x in np.linspace(0.2, ext[0] - 0.1, 13)])
+    wav = np.stack([wl.ricker(nt, dt, 25.0), 0.5 * wl.ricker(nt, dt, 18.0)], 1)
+    return dict(n=n, h=h, space_order=so, nbl=nbl, dt=dt, nt=nt, v=v, src=src, rec=rec,
+                wavelet=np.ascontiguousarray(wav, np.float32))
+
+
+def test_small_acoustic_64(fd):
+    w = wl.small_acoustic(64)
+    rec, u = run_gpu(fd, w)
+    rrec, ru = run_oracle(w)
+    assert rel(rec, rrec) <= TOL
+    assert rel(u, ru) <= TOL
+
+
+@pytest.mark.parametrize("so", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_every_space_order_on_a_ragged_grid(fd, so):
+    w = ragged_workload(so)
+    rec, u = run_gpu(fd, w)
+    rrec, ru = run_oracle(w)
+    assert rel(rec, rrec) <= TOL, rel(rec, rrec)
+    assert rel(u, ru) <= TOL, rel(u, ru)
+
+
+@pytest.mark.parametrize("so", [4, 8, 16])
+def test_tile_shapes_and_z_split_agree_bitwise(fd, so):
+    w = ragged_workload(so, n=(70, 45, 41), nbl=6, nt=25)
+    ref_rec, ref_u = run_gpu(fd, w, tile=(64, 16), zsplit=1)
+    orec, ou = run_oracle(w)
+    assert rel(ref_rec, orec) <= TOL and rel(ref_u, ou) <= TOL
+    for tile in [(64, 16), (128, 8), (32, 32), (64, 8)]:
+        for zsplit in (1, 3, 7):
+            rec, u = run_gpu(fd, w, tile=tile, zsplit=zsplit)
+            np.testing.assert_array_equal(rec, ref_rec)
+            np.testing.assert_array_equal(u, ref_u)
+
+
+def test_single_step_from_random_state_elementwise(fd):
+    w = ragged_workload(8, n=(45, 33, 27), nbl=7)
+    og = oracle_grid(w)
+    shp = og.padded_shape
+    up = wl.random_state(shp, 11).astype(np.float32)
+    uc = wl.random_state(shp, 12).astype(np.float32)
+    m = 1.0 / w["v"].astype(np.float64) ** 2
+    ref, _ = oracle.step(og, oracle.pad_model(og, m), oracle.damping(og, float(w["v"].max())),
+                         up, uc)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        g.set_wavefield(up, uc)
+        fd.check(g.propagate(0, 1), "fd_propagate")
+        p2 = np.zeros(shp, np.float32)
+        c2 = np.zeros(shp, np.float32)
+        g.get_wavefield(p2, c2)
+    np.testing.assert_array_equal(p2, uc)  # the old u^n becomes u^{n-1}
+    scale = np.abs(ref).max()
+    assert np.abs(c2 - ref).max() <= 2e-6 * scale
+
+
+def test_full_size_512_single_step_sampled(fd):
+    """The headline grid (512^3 + 40-cell layer, SO 8) in the benchmark's
+    launch configuration: one step from a random state, compared with the
+    oracle at 40k sampled points (all corners, faces, tile and layer seams)."""
+    w = wl.acoustic_512()
+    og = oracle_grid(w)
+    shp = og.padded_shape
+    up = wl.random_state(shp, 21).astype(np.float32)
+    uc = wl.random_state(shp, 22).astype(np.float32)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        info = g.info()
+        g.set_wavefield(up, uc)
+        fd.check(g.propagate(0, 1), "fd_propagate")
+        out = np.zeros(shp, np.float32)
+        g.get_wavefield(None, out)
+    Nz, Ny, Nx = shp
+    rng = np.random.default_rng(3)
+    pts = [rng.integers(0, s, 30000) for s in (Nz, Ny, Nx)]
+    seams = []
+    for ax_vals in ([0, 1, 3, 4, 5, 39, 40, 41, 295, 296, 551, 552, Nz - 2, Nz - 1],):
+        for z in ax_vals:
+            for y in ax_vals:
+                for x in list(ax_vals) + [info["tile_x"] * k + d for k in (1, 4, 8)
+                                          for d in (-1, 0)]:
+                    seams.append((z, y, min(x, Nx - 1)))
+    seams = np.array(seams).T
+    z = np.concatenate([pts[0], seams[0]])
+    y = np.concatenate([pts[1], seams[1]])
+    x = np.concatenate([pts[2], seams[2]])
+    idx = (z * Ny + y) * Nx + x
+    m = 1.0 / w["v"].astype(np.float64) ** 2
+    ref = oracle.step_points(og, m, float(w["v"].max()), up, uc, idx)
+    got = out.ravel()[idx]
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_host_and_device_buffers_give_identical_results(fd):
+    import torch
+    w = ragged_workload(8, nt=30)
+    rec_h, u_h = run_gpu(fd, w)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(torch.from_numpy(w["v"]).cuda())
+        wav = torch.from_numpy(w["wavelet"]).cuda()
+        rec = torch.zeros((w["nt"], len(w["rec"])), device="cuda")
+        u = torch.zeros(g.phys_shape, device="cuda")
+        fd.check(g.forward(w["src"], wav, w["rec"], rec, u), "fd_forward")
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(rec.cpu().numpy(), rec_h)
+    np.testing.assert_array_equal(u.cpu().numpy(), u_h)
+
+
+def test_propagate_in_pieces_equals_one_run(fd):
+    w = ragged_workload(6, nt=30)
+    rec_full, u_full = run_gpu(fd, w)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        a = np.zeros((11, len(w["rec"])), np.float32)
+        b = np.zeros((19, len(w["rec"])), np.float32)
+        fd.check(g.propagate(0, 11, w["src"], w["wavelet"][:11], w["rec"], a), "p1")
+        fd.check(g.propagate(11, 19, w["src"], w["wavelet"], w["rec"], b), "p2")
+        u = np.zeros(g.phys_shape, np.float32)
+        g.get_wavefield(None, u, fd.FD_REGION_PHYSICAL)
+    np.testing.assert_array_equal(np.concatenate([a, b]), rec_full)
+    np.testing.assert_array_equal(u, u_full)
+
+
+def test_graph_and_direct_launches_agree(fd):
+    w = ragged_workload(4, nt=20)
+    rec_g, u_g = run_gpu(fd, w)
+    with fd.Grid.from_workload(w) as g:
+        g.set_debug(fd.FD_DEBUG_NO_GRAPH, 1)
+        g.set_model(w["v"])
+        rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        u = np.zeros(g.phys_shape, np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec, u), "fd_forward")
+    np.testing.assert_array_equal(rec, rec_g)
+    np.testing.assert_array_equal(u, u_g)
+
+
+def test_repeated_forward_reuses_graph_and_matches(fd):
+    w = ragged_workload(8, nt=15)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        outs = []
+        for _ in range(3):
+            rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+            fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec), "fd_forward")
+            outs.append(rec)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+def test_empty_point_sets_and_zero_steps(fd):
+    w = ragged_workload(4, nt=10)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        fd.check(g.forward(np.zeros((0, 3)), None, np.zeros((0, 3)), None), "no points")
+        u = np.ones(g.phys_shape, np.float32)
+        g.get_wavefield(None, u, fd.FD_REGION_PHYSICAL)
+        assert not u.any()
+        fd.check(g.propagate(0, 0), "zero steps")
+
+
+def test_degenerate_one_cell_grid_without_layer(fd):
+    w = dict(n=(1, 1, 1), h=10.0, space_order=8, nbl=0, dt=1.0, nt=12,
+             v=np.full((1, 1, 1), 2.0, np.float32), src=np.zeros((1, 3)),
+             rec=np.zeros((1, 3)), wavelet=wl.ricker(12, 1.0, 50.0).reshape(12, 1))
+    rec, u = run_gpu(fd, w)
+    rrec, ru = run_oracle(w)
+    assert rel(rec, rrec) <= TOL and rel(u, ru) <= TOL
