@@ -316,8 +316,157 @@ def run_ours(args, w, world, rank, local):
         dist.destroy_process_group()
 
 
+def _device_ms(fn, stream, reps):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_adjoint(args):
+    """Time to gradient of the 256^3 (+20) SO 8 500-step case with 25
+    checkpoints; roofline against 64 B per point-step (forward 16, recompute
+    with e 20, adjoint with imaging 28)."""
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    from paper_2312_13094_gb300 import workloads as wl
+    import oracle  # noqa: F401  (oracle only for the observed data below)
+    w = wl.adjoint_256(n=args.n if args.n != 512 else 256, nt=args.nt if args.nt != 1000 else 500)
+    w0 = wl.adjoint_256(n=w["n"][0], nt=w["nt"], anomaly=False)
+    stream = torch.cuda.Stream()
+    npts = int(np.prod(_padded(w)))
+    with torch.cuda.stream(stream):
+        g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
+        g.set_model(w["v"])
+        d_obs = torch.zeros((w["nt"], len(w["rec"])), device="cuda")
+        wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+        fd.check(g.forward(w["src"], wav, w["rec"], d_obs), "observed data")
+        g.set_model(w0["v"])
+        grad = torch.zeros(g.phys_shape, device="cuda")
+
+        def one():
+            st, _ = g.adjoint_gradient(w["src"], wav, w["rec"], d_obs, 25, grad)
+            fd.check(st, "fd_adjoint_gradient")
+
+        for _ in range(args.warmup):
+            one()
+        ms = _device_ms(one, stream, args.steps)
+        g.close()
+    gbs = 64 * npts * w["nt"] / (ms * 1e-3) / 1e9
+    peak, kind = _peaks()
+    print(json.dumps({"metric": "time to gradient", "value": ms / 1e3, "unit": "s",
+                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": w["name"], "grid_padded": _padded(w),
+                                 "checkpoints": 25},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
+                                   "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
+                                   "algorithmic_bytes_per_point_step": 64}}), flush=True)
+
+
+def run_batched(args):
+    """32 uneven shots, 600 steps: aggregate Gpts/s of fd_batch_forward
+    (persistent launch per step + graph + autotuned tiles) and of 32
+    sequential fd_forward calls."""
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    from paper_2312_13094_gb300 import workloads as wl
+    shots = wl.batched_shots(nt=args.nt if args.nt != 1000 else 600)
+    stream = torch.cuda.Stream()
+    pts = sum(int(np.prod(_padded(w))) for w in shots)
+    nt = shots[0]["nt"]
+    os.environ.setdefault("FD_AUTOTUNE_CACHE", os.path.join(ROOT, "gpurun_out", "autotune.txt"))
+    with torch.cuda.stream(stream):
+        grids, spec = [], []
+        for w in shots:
+            g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
+            g.set_model(w["v"])
+            rec = torch.zeros((nt, len(w["rec"])), device="cuda")
+            wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+            grids.append(g)
+            spec.append((g, w["src"], wav, w["rec"], rec))
+
+        def batch():
+            fd.check(fd.batch_forward(spec, fd.FD_BATCH_GRAPH | fd.FD_BATCH_AUTOTUNE),
+                     "fd_batch_forward")
+
+        def sequential():
+            for g, src, wav, rec, out in spec:
+                fd.check(g.forward(src, wav, rec, out), "fd_forward")
+
+        for _ in range(args.warmup):
+            batch()
+        ms_b = _device_ms(batch, stream, args.steps)
+        info = grids[0].info()
+        sequential()
+        ms_s = _device_ms(sequential, stream, 1)
+        for g in grids:
+            g.close()
+    peak, kind = _peaks()
+    gbs = 16 * pts * nt / (ms_b * 1e-3) / 1e9
+    print(json.dumps({"metric": "Gpts/s", "value": pts * nt / (ms_b * 1e-3) / 1e9,
+                      "unit": "Gpts/s", "higher_is_better": True, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms_b, "dtype": "f32",
+                      "data": "synthetic",
+                      "config": {"workload": "32 shots 128..320^3 (+20) SO8 600 steps",
+                                 "points": pts, "tile": [info["tile_x"], info["tile_y"],
+                                                         info["zsplit"]]},
+                      "sequential_gpts": pts * nt / (ms_s * 1e-3) / 1e9,
+                      "speedup_vs_sequential": ms_s / ms_b,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
+                                   "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind}}),
+          flush=True)
+
+
+def run_learned(args):
+    """Learned per-cell SO 8 weights on the coarse grid vs the plain SO 16
+    fine solve: train on fine-run samples of `--train-models` models, then
+    compare receivers and GPU times on `--test-models` held-out models."""
+    import torch
+    from paper_2312_13094_gb300 import learned as lr
+    n, nt = args.n, (args.nt if args.nt != 1000 else 1250)
+    t0 = time.time()
+    data = []
+    for s in range(args.train_models):
+        fine, coarse = lr.pair(s, n=n, nt=nt)
+        data.append(lr.training_samples(fine, coarse, ncell=16384, ntimes=8, seed=s))
+    S = torch.cat(data)
+    S = S[torch.randperm(S.shape[0], generator=torch.Generator().manual_seed(0)).to(S.device)]
+    t_data = time.time() - t0
+    net = lr.Network(lr.init_params(0, scale_out=0.0))
+    l0 = net.loss_grad(S)[0]
+    t1 = time.time()
+    l1 = net.train(S, epochs=args.epochs, batch=65536, lr=1e-3)
+    t_train = time.time() - t1
+    rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt)
+    np.save(os.path.join(ROOT, "gpurun_out", "learned_params.npy"), net.params())
+    plain = float(np.mean([r["plain"] for r in rows]))
+    learned = float(np.mean([r["learned"] for r in rows]))
+    print(json.dumps({
+        "metric": "receiver rel. L2 vs fine SO16 (learned coarse)", "value": learned,
+        "unit": "rel. L2", "higher_is_better": False, "plain_coarse": plain,
+        "ms_fine": float(np.mean([r["ms_fine"] for r in rows])),
+        "ms_coarse_plain": float(np.mean([r["ms_plain"] for r in rows])),
+        "ms_coarse_learned": float(np.mean([r["ms_learned"] for r in rows])),
+        "loss_before": l0, "loss_after": l1, "samples": int(S.shape[0]),
+        "train_models": args.train_models, "test_models": args.test_models,
+        "epochs": args.epochs, "data_s": t_data, "train_s": t_train, "rows": rows,
+        "config": {"workload": f"fine {n}^3 h10 SO16 dt0.8 {nt} steps vs coarse "
+                               f"{n // 2}^3 h20 SO8 dt1.6"}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "adjoint", "batched", "learned"])
+    ap.add_argument("--train-models", type=int, default=48)
+    ap.add_argument("--test-models", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -329,6 +478,12 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     args = ap.parse_args()
     world, rank, local = _dist()
+    if args.workload != "headline":
+        import torch
+        torch.cuda.set_device(local)
+        {"adjoint": run_adjoint, "batched": run_batched, "learned": run_learned}[
+            args.workload](args)
+        return
     from paper_2312_13094_gb300 import workloads as wl
     w = wl.acoustic_512(n=args.n, nt=args.nt)
     if args.impl == "reference":

@@ -623,7 +623,7 @@ fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
   g->ncell = size_t(g->pitch) * g->Ny * g->Nz;
   fd_weights(g->R, g->c);
   g->cfl = cfl_limit(g->c, g->R);
-  g->spin_limit = 4000000000LL;  // ~2 s at 2 GHz
+  g->spin_limit = 200000000LL;  // ~0.1 s at 2 GHz; a tile load takes microseconds
   if (const char* s = getenv("FD_SPIN_LIMIT")) g->spin_limit = atoll(s);
   set_shape(g, default_shape(g->R, g->Nx, g->Ny, g->Nz));
 

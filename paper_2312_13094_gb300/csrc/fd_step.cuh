@@ -142,6 +142,13 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const int zl = zend - zbeg;
   const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
   const long long limit = a.spin_limit;
+  // once any CTA has recorded a failed wait, later columns and launches of
+  // the same run return at once instead of waiting again (read by one
+  // thread and shared, so the whole CTA takes the same branch)
+  __shared__ int s_abort;
+  if (tid == 0) s_abort = *reinterpret_cast<volatile const int*>(a.err);
+  __syncthreads();
+  if (s_abort) return;
 
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar_u0 = sbase + C::OFF_BAR;
@@ -164,7 +171,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     if (j >= J) return;
     ju_next = j + 1;
     const int z = zbeg - R + j;
-    if (z == a.debug_skip_plane) return;
+    if (a.debug_skip_plane >= 0 && z == a.debug_skip_plane) return;
     const int slot = j % C::SU;
     const uint32_t bar = bar_u0 + 8 * slot;
     mbar_expect_tx(bar, C::UBYTES);
@@ -384,7 +391,7 @@ fail:
     atomicOr(a.err, 1);
     // wait (bounded) for every copy this CTA still has in flight
     for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
-      if (zbeg - R + j == a.debug_skip_plane) continue;
+      if (a.debug_skip_plane >= 0 && zbeg - R + j == a.debug_skip_plane) continue;
       mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, limit);
     }
     for (int i = max(0, ia_next - C::SA); i < ia_next; ++i)

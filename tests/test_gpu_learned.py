@@ -1,0 +1,170 @@
+"""Learned per-cell weights on the GPU: network inference, loss gradient and
+Adam against the FP64 reference network; the per-cell stencil against the
+oracle; and the trained network's gain over the plain coarse stencil.
+
+Tolerances: inference and loss rel. 1e-5 (FP32 dense layers of width 64);
+gradient rel. L2 1e-4 (FP32 sums over the samples of a batch).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2312_13094_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2312_13094_gb300 import build
+    build.build()
+    from paper_2312_13094_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def learned(fd):
+    from paper_2312_13094_gb300 import learned as lr
+    return lr
+
+
+def samples(n, seed):
+    rng = np.random.default_rng(seed)
+    X = mlp.features(rng.uniform(1.5, 4.5, n), 20.0, 1.6, 12.0)
+    T = rng.standard_normal((n, 4))
+    y = rng.standard_normal(n) * 0.3
+    w = rng.uniform(0.5, 2.0, n)
+    return np.ascontiguousarray(np.concatenate([X, T, y[:, None], w[:, None]], 1), np.float32)
+
+
+def test_inference_matches_reference(learned):
+    th = mlp.init_params(5, scale_out=0.8).astype(np.float32)
+    net = learned.Network(th)
+    X = mlp.features(np.linspace(1.5, 4.5, 301), 20.0, 1.6, 12.0).astype(np.float32)
+    got = net.coefficients(X)
+    ref = mlp.coefficients(th.astype(np.float64), X.astype(np.float64), oracle.fd_coefficients(4))
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    net.close()
+
+
+@pytest.mark.parametrize("n", [1, 127, 1000, 5003])
+def test_loss_gradient_matches_reference(learned, n):
+    th = mlp.init_params(6, scale_out=0.8).astype(np.float32)
+    net = learned.Network(th)
+    S = samples(n, n)
+    loss, g = net.loss_grad(S)
+    rl, rg = mlp.loss_grad(th.astype(np.float64), S.astype(np.float64),
+                           oracle.fd_coefficients(4))
+    assert abs(loss - rl) <= 1e-5 * abs(rl)
+    assert np.linalg.norm(g - rg) <= 1e-4 * np.linalg.norm(rg)
+    net.close()
+
+
+def test_adam_step_matches_reference(fd, learned):
+    th = mlp.init_params(7, scale_out=0.8).astype(np.float32)
+    net = learned.Network(th)
+    S = samples(777, 8)
+    ref = th.astype(np.float64)
+    m = np.zeros_like(ref)
+    v = np.zeros_like(ref)
+    for t in range(1, 4):
+        _, g = net.loss_grad(S)
+        fd.check(fd.fd_mlp_adam_step(net.handle, 1e-3), "adam")
+        _, rg = mlp.loss_grad(ref, S.astype(np.float64), oracle.fd_coefficients(4))
+        ref, m, v = mlp.adam(ref, rg, m, v, t, lr=1e-3)
+    assert np.abs(net.params() - ref).max() <= 2e-6
+    net.close()
+
+
+def _percell_workload(nt=40):
+    n = (30, 26, 22)
+    h = 20.0
+    v = wl.layered_model(n, h, 23, vmin=1.5, vmax=4.5)
+    dt = 0.3 * h / 4.5
+    ext = [(d - 1) * h for d in n]
+    src = np.array([[0.5 * ext[0], 0.5 * ext[1], 0.3 * ext[2]]])
+    rec = np.array([[x, 0.5 * ext[1], 0.8 * ext[2]] for x in np.linspace(0, ext[0], 9)])
+    return dict(n=n, h=h, space_order=8, nbl=6, dt=dt, nt=nt, v=v, src=src, rec=rec,
+                wavelet=wl.ricker(nt, dt, 12.0).reshape(nt, 1), f0=12.0)
+
+
+def _oracle_percell(w, c_pad):
+    og = oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=4, nbl=w["nbl"])
+    pc = np.zeros(og.padded_shape + (5,))
+    pc[..., 1:] = c_pad
+    pc[..., 0] = -2.0 * c_pad.sum(-1)
+    out = oracle.forward(og, 1.0 / w["v"].astype(np.float64) ** 2, w["nt"], w["src"],
+                         w["wavelet"], w["rec"], percell=pc.reshape(-1, 5))
+    return og, out["rec"]
+
+
+def test_per_cell_weights_match_oracle(fd):
+    w = _percell_workload()
+    rng = np.random.default_rng(1)
+    cT = oracle.fd_coefficients(4)
+    cphys = (cT[1:] * (1 + 0.2 * rng.uniform(-1, 1, w["v"].shape + (4,)))).astype(np.float32)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        fd.check(fd.fd_set_coefficients(g.handle, cphys.ctypes.data, fd.FD_COEF_PER_CELL),
+                 "per-cell")
+        rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec), "fd_forward")
+    og = oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=4, nbl=w["nbl"])
+    Nz, Ny, Nx = og.padded_shape
+    nb = w["nbl"]
+    iz = np.clip(np.arange(Nz) - nb, 0, w["n"][2] - 1)
+    iy = np.clip(np.arange(Ny) - nb, 0, w["n"][1] - 1)
+    ix = np.clip(np.arange(Nx) - nb, 0, w["n"][0] - 1)
+    c_pad = cphys.astype(np.float64)[iz][:, iy][:, :, ix]
+    _, ref = _oracle_percell(w, c_pad)
+    assert np.linalg.norm(rec - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_learned_weights_on_a_grid_match_oracle(fd, learned):
+    w = _percell_workload()
+    th = mlp.init_params(9, scale_out=1.0).astype(np.float32)
+    net = learned.Network(th)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        fd.check(fd.fd_set_learned_coefficients(g.handle, net.handle, w["f0"]), "learned")
+        rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec), "fd_forward")
+    og = oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=4, nbl=w["nbl"])
+    v_pad = 1.0 / np.sqrt(oracle.pad_model(og, 1.0 / w["v"].astype(np.float64) ** 2))
+    X = mlp.features(v_pad, w["h"], w["dt"], w["f0"]).reshape(-1, 4)
+    c_pad = mlp.coefficients(th.astype(np.float64), X, oracle.fd_coefficients(4))
+    _, ref = _oracle_percell(w, c_pad.reshape(og.padded_shape + (4,)))
+    assert np.linalg.norm(rec - ref) / np.linalg.norm(ref) <= 1e-5
+    net.close()
+
+
+def test_training_improves_the_coarse_solve(learned):
+    """Small fine/coarse pair (fine 96^3 SO 16, coarse 48^3 SO 8 at twice h
+    and dt): after training on fine-run samples of other models, the learned
+    coarse receivers are closer to the fine ones than the plain SO 8 coarse
+    receivers on held-out models."""
+    kw = dict(n=96, nt=400, nbl=16, f_hz=22.0, nrec=40)
+    data = []
+    for s in range(6):
+        fine, coarse = learned.pair(100 + s, **kw)
+        data.append(learned.training_samples(fine, coarse, ncell=8192, ntimes=6, seed=s))
+    import torch
+    S = torch.cat(data)
+    S = S[torch.randperm(S.shape[0], generator=torch.Generator().manual_seed(0)).to(S.device)]
+    net = learned.Network(learned.init_params(0, scale_out=0.0))
+    l0 = net.loss_grad(S)[0]
+    l1 = net.train(S, epochs=30, batch=8192, lr=2e-3)
+    assert l1 < 0.7 * l0, (l0, l1)
+    gains = []
+    for s in (200, 201):
+        fine, coarse = learned.pair(s, **kw)
+        ref = learned.run_forward(fine)[0][::2]
+        plain = learned.rel_l2(learned.run_forward(coarse)[0], ref)
+        lrn = learned.rel_l2(learned.run_forward(coarse, net=net.handle)[0], ref)
+        gains.append((plain, lrn))
+    assert all(l < p for p, l in gains), gains
+    net.close()
