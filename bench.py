@@ -295,7 +295,7 @@ def run_ours(args, w, world, rank, local):
                      "avg_launch_ms": avg_launch_ms},
         "clocks": clk,
         "gpu_launches": int(launches),
-        "tile": [info["tile_x"], info["tile_y"], info["zsplit"]],
+        "tile": [info["tile_x"], info["tile_y"], info["ctas"]],
         "interior_gpts": world * int(np.prod(w["n"])) * nt * args.steps /
         (ms_max * 1e-3) / 1e9,
         "paper_context": {"value": 31.2, "unit": "Gpts/s",
@@ -415,7 +415,7 @@ def run_batched(args):
                       "data": "synthetic",
                       "config": {"workload": "32 shots 128..320^3 (+20) SO8 600 steps",
                                  "points": pts, "tile": [info["tile_x"], info["tile_y"],
-                                                         info["zsplit"]]},
+                                                         info["ctas"]]},
                       "sequential_gpts": pts * nt / (ms_s * 1e-3) / 1e9,
                       "speedup_vs_sequential": ms_s / ms_b,
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,

@@ -86,7 +86,7 @@ typedef struct {
 typedef struct {
   int32_t nx_pad, ny_pad, nz_pad; /* padded (physical + 2 nbl) extents */
   int32_t pitch;                  /* floats between rows of device arrays */
-  int32_t tile_x, tile_y, zsplit; /* stencil tile chosen for this grid */
+  int32_t tile_x, tile_y, ctas;   /* stencil tile and persistent CTAs per sweep */
   double v_max;                   /* from the model, km/s */
   double cfl_limit;               /* largest stable v_max dt / h */
   int64_t launches;               /* library kernels launched so far */
@@ -163,10 +163,12 @@ typedef struct {
 fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
                            int32_t flags);
 
-/* Chooses the stencil tile (tile_x x tile_y points per CTA, z split into
- * `zsplit` chunks).  Compiled tiles: 64x16, 128x8, 32x32, 64x8.
- * Errors: FD_ERR_ARG for a tile that is not compiled or zsplit < 1. */
-fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t zsplit);
+/* Chooses the stencil tile (tile_x x tile_y points per CTA column) and the
+ * number of persistent CTAs of each step launch (0: as many as are resident
+ * on all SMs at once).  Each CTA sweeps an equal contiguous share of the
+ * grid's (tile, z plane) units.  Compiled tiles: 64x16, 128x8, 32x32, 64x8.
+ * Errors: FD_ERR_ARG for a tile that is not compiled or ctas < 0. */
+fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas);
 
 /* Test hooks, host-side fault injection only:
  *   FD_DEBUG_SKIP_PLANE  value z >= 0: the first step of the next run never

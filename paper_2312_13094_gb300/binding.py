@@ -53,7 +53,7 @@ class fd_grid_info(ctypes.Structure):
     _fields_ = [("nx_pad", ctypes.c_int32), ("ny_pad", ctypes.c_int32),
                 ("nz_pad", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("zsplit", ctypes.c_int32), ("v_max", ctypes.c_double),
+                ("ctas", ctypes.c_int32), ("v_max", ctypes.c_double),
                 ("cfl_limit", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("step_ms", ctypes.c_double), ("steps_timed", ctypes.c_int64)]
 
@@ -214,8 +214,8 @@ class Grid:
     def set_model(self, data, kind=FD_MODEL_VP_KMS):
         check(fd_set_model(self.handle, _ptr(data), kind), "fd_set_model")
 
-    def set_tile(self, tile_x, tile_y, zsplit=1):
-        check(fd_set_tile(self.handle, tile_x, tile_y, zsplit), "fd_set_tile")
+    def set_tile(self, tile_x, tile_y, ctas=0):
+        check(fd_set_tile(self.handle, tile_x, tile_y, ctas), "fd_set_tile")
 
     def set_debug(self, key, value):
         check(fd_set_debug(self.handle, key, value), "fd_set_debug")

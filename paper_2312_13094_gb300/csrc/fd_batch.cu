@@ -1,8 +1,10 @@
 // Batched multi-shot forward modelling: every time step of all shots is one
-// persistent launch over a shared work list, and the nt launches are captured
-// in one CUDA graph.  A tile autotuner times the compiled tile shapes on the
-// actual batch once per (GPU, space order, window sizes) and caches the pick
-// in memory and, if FD_AUTOTUNE_CACHE names a file, on disk.
+// persistent sweep launch over the concatenated (shot, tile, plane) units of
+// the batch, each resident CTA taking an equal contiguous share, and the nt
+// launches are captured in one CUDA graph.  A tile autotuner times the
+// compiled tile shapes on the actual batch once per (GPU, space order, window
+// sizes) and caches the pick in memory and, if FD_AUTOTUNE_CACHE names a
+// file, on disk (the paper tunes loop blocking the same way, Sec. IV-C).
 #include <string.h>
 
 #include <algorithm>
@@ -19,45 +21,15 @@ using namespace fd;
 namespace {
 
 struct BatchWorkspace {
-  DevBuf shots, work, counters;
+  DevBuf desc;  // ShotDesc[nshots] followed by the unit prefix [nshots + 1]
   bool graph_valid = false;
   cudaGraphExec_t gexec = nullptr;
   std::vector<char> key;
 };
 
 std::mutex g_mu;
-std::map<int, BatchWorkspace> g_ws;           // per device
-std::map<std::string, TileShape> g_tuned;     // autotuner picks
-
-cudaError_t launch_batch(int R, const TileShape& t, const BatchShot* shots, const int4* work,
-                         int nwork, int* counter, int step, int grid, cudaStream_t s) {
-  count_launch();
-  switch (R) {
-    case 1: return launch_batch_r<1>(t, shots, work, nwork, counter, step, grid, s);
-    case 2: return launch_batch_r<2>(t, shots, work, nwork, counter, step, grid, s);
-    case 3: return launch_batch_r<3>(t, shots, work, nwork, counter, step, grid, s);
-    case 4: return launch_batch_r<4>(t, shots, work, nwork, counter, step, grid, s);
-    case 5: return launch_batch_r<5>(t, shots, work, nwork, counter, step, grid, s);
-    case 6: return launch_batch_r<6>(t, shots, work, nwork, counter, step, grid, s);
-    case 7: return launch_batch_r<7>(t, shots, work, nwork, counter, step, grid, s);
-    case 8: return launch_batch_r<8>(t, shots, work, nwork, counter, step, grid, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-int blocks_per_sm(int R, const TileShape& t) {
-  switch (R) {
-    case 1: return batch_blocks_per_sm_r<1>(t);
-    case 2: return batch_blocks_per_sm_r<2>(t);
-    case 3: return batch_blocks_per_sm_r<3>(t);
-    case 4: return batch_blocks_per_sm_r<4>(t);
-    case 5: return batch_blocks_per_sm_r<5>(t);
-    case 6: return batch_blocks_per_sm_r<6>(t);
-    case 7: return batch_blocks_per_sm_r<7>(t);
-    case 8: return batch_blocks_per_sm_r<8>(t);
-  }
-  return 0;
-}
+std::map<int, BatchWorkspace> g_ws;        // per device
+std::map<std::string, TileShape> g_tuned;  // autotuner picks
 
 std::string tune_key(int device, int R, int nshots, const fd_shot* shots) {
   cudaDeviceProp p;
@@ -86,7 +58,7 @@ void load_cache_file() {
   if (!f) return;
   char key[4096];
   TileShape t;
-  while (fscanf(f, "%4095s %d %d %d %d", key, &t.tx, &t.ty, &t.pf, &t.zsplit) == 5)
+  while (fscanf(f, "%4095s %d %d %d %d", key, &t.tx, &t.ty, &t.pf, &t.ctas) == 5)
     g_tuned[key] = t;
   fclose(f);
 }
@@ -96,32 +68,32 @@ void save_cache_entry(const std::string& key, const TileShape& t) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.tx, t.ty, t.pf, t.zsplit);
+  fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.tx, t.ty, t.pf, t.ctas);
   fclose(f);
 }
 
 struct Prepared {
-  std::vector<BatchShot> hs;
-  std::vector<int4> work;
+  std::vector<char> host;  // descriptors + prefix, as uploaded
   std::vector<float*> drec;
-  int nwork = 0;
-  int grid = 0;
+  int nshots = 0;
+  int ctas = 0;
 };
 
-// Puts every shot on tile shape t and builds the device descriptors and the
-// longest-first work list.
+// Puts every shot on tile shape t and builds the descriptors and the unit
+// prefix of the batch.
 fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared& P) {
   const int R = shots[0].grid->R;
-  P.hs.assign(nshots, BatchShot());
+  P.nshots = nshots;
   P.drec.assign(nshots, nullptr);
-  std::vector<std::pair<int, int4>> items;
+  P.host.assign(nshots * sizeof(ShotDesc) + (nshots + 1) * sizeof(long long), 0);
+  ShotDesc* desc = reinterpret_cast<ShotDesc*>(P.host.data());
+  long long* prefix = reinterpret_cast<long long*>(P.host.data() + nshots * sizeof(ShotDesc));
+  prefix[0] = 0;
   for (int i = 0; i < nshots; ++i) {
     fd_grid g = shots[i].grid;
     const TileShape old = g->shape;
-    if (old.tx != t.tx || old.ty != t.ty || old.pf != t.pf || old.zsplit != t.zsplit) {
-      TileShape tt = t;
-      tt.zsplit = std::min(t.zsplit, g->Nz);
-      set_shape(g, tt);
+    if (old.tx != t.tx || old.ty != t.ty || old.ctas != t.ctas) {
+      set_shape(g, t);
       fd_status st = build_maps(g);
       if (st) return st;
     }
@@ -138,60 +110,34 @@ fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared
                         size_t(g->d.nt) * nrec, &drec)))
       return st;
     P.drec[i] = drec;
-    BatchShot& b = P.hs[i];
-    memset(&b, 0, sizeof(b));
-    for (int k = 0; k < 2; ++k) {
-      b.halo[k] = g->F.halo[k];
-      b.tile[k] = g->F.tile[k];
-      b.u[k] = g->F.u[k];
-    }
-    b.A = g->mapA;
-    b.args = base_args(g);
+    RunSpec rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.f = &g->F;
     if (nsrc) {
-      b.args.inj_start = static_cast<const int32_t*>(g->tab.inj_start.p);
-      b.args.inj = static_cast<const InjEntry*>(g->tab.inj.p);
-      b.args.inj_val = dval;
-      b.args.inj_ncol = nsrc;
+      rs.inj_start = static_cast<const int32_t*>(g->tab.inj_start.p);
+      rs.inj = static_cast<const InjEntry*>(g->tab.inj.p);
+      rs.inj_val = dval;
+      rs.inj_ncol = nsrc;
     }
     if (nrec) {
-      b.args.rec_start = static_cast<const int32_t*>(g->tab.rec_start.p);
-      b.args.recs = static_cast<const RecEntry*>(g->tab.recs.p);
-      b.args.rec_out = drec;
-      b.args.rec_ncol = nrec;
+      rs.rec_start = static_cast<const int32_t*>(g->tab.rec_start.p);
+      rs.recs = static_cast<const RecEntry*>(g->tab.recs.p);
+      rs.rec_out = drec;
+      rs.rec_ncol = nrec;
     }
-    for (int zc = 0; zc < g->shape.zsplit; ++zc) {
-      const int zl = std::min(g->Nz, (zc + 1) * g->zlen) - zc * g->zlen;
-      if (zl <= 0) continue;
-      for (int ty = 0; ty < g->tiles_y; ++ty)
-        for (int tx = 0; tx < g->tiles_x; ++tx)
-          items.push_back({zl + 2 * R, make_int4(i, tx, ty, zc)});
-    }
+    fill_desc(g, rs, &desc[i]);
+    prefix[i + 1] = prefix[i] + (long long)g->tiles_x * g->tiles_y * g->Nz;
   }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const auto& a, const auto& b) { return a.first > b.first; });
-  P.work.clear();
-  for (auto& it : items) P.work.push_back(it.second);
-  P.nwork = int(P.work.size());
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per = std::max(1, blocks_per_sm(R, t));
-  P.grid = std::max(1, std::min(P.nwork, per * sms));
+  P.ctas = sweep_ctas(R, t, kModeForward);
   return FD_OK;
 }
 
-fd_status upload_prepared(BatchWorkspace& ws, const Prepared& P, int nt, cudaStream_t s) {
-  cudaError_t e = ws.shots.ensure(P.hs.size() * sizeof(BatchShot));
-  if (!e) e = ws.work.ensure(std::max<size_t>(P.work.size() * sizeof(int4), 16));
-  if (!e) e = ws.counters.ensure(size_t(std::max(nt, 1)) * sizeof(int));
-  if (e) return cuda_fail(e, "batch workspace allocation");
-  e = cudaMemcpyAsync(ws.shots.p, P.hs.data(), P.hs.size() * sizeof(BatchShot),
-                      cudaMemcpyHostToDevice, s);
-  if (!e && !P.work.empty())
-    e = cudaMemcpyAsync(ws.work.p, P.work.data(), P.work.size() * sizeof(int4),
-                        cudaMemcpyHostToDevice, s);
+fd_status upload_prepared(BatchWorkspace& ws, const Prepared& P, cudaStream_t s) {
+  cudaError_t e = ws.desc.ensure(P.host.size());
+  if (e) return cuda_fail(e, "batch descriptor allocation");
+  e = cudaMemcpyAsync(ws.desc.p, P.host.data(), P.host.size(), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaStreamSynchronize(s);
-  if (e) return cuda_fail(e, "batch workspace upload");
+  if (e) return cuda_fail(e, "batch descriptor upload");
   return FD_OK;
 }
 
@@ -210,12 +156,16 @@ fd_status zero_state(int nshots, const fd_shot* shots, cudaStream_t s) {
 // Issues steps [0, nsteps) of the prepared batch on stream s.
 fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileShape& t,
                       int nsteps, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ws.counters.p, 0, size_t(nsteps) * sizeof(int), s);
-  if (e) return cuda_fail(e, "counter reset");
+  const ShotDesc* d = static_cast<const ShotDesc*>(ws.desc.p);
+  const long long* prefix = reinterpret_cast<const long long*>(
+      static_cast<const char*>(ws.desc.p) + P.nshots * sizeof(ShotDesc));
   for (int step = 0; step < nsteps; ++step) {
-    e = launch_batch(R, t, static_cast<const BatchShot*>(ws.shots.p),
-                     static_cast<const int4*>(ws.work.p), P.nwork,
-                     static_cast<int*>(ws.counters.p) + step, step, P.grid, s);
+    StepOverride ov;
+    memset(&ov, 0, sizeof(ov));
+    ov.cur = step & 1;
+    ov.inj_row = step;
+    ov.rec_row = step;
+    cudaError_t e = launch_sweep(R, t, kModeForward, d, prefix, P.nshots, ov, P.ctas, s);
     if (e) return cuda_fail(e, "batch launch");
   }
   return FD_OK;
@@ -228,39 +178,33 @@ fd_status autotune(BatchWorkspace& ws, int nshots, const fd_shot* shots, int R, 
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  for (int i = 0; i < kNumShapes; ++i) {
-    for (int zs : {1, 2}) {
-      TileShape t = kShapes[i];
-      t.zsplit = zs;
-      Prepared P;
-      fd_status st = prepare(nshots, shots, t, P);
-      if (!st) st = upload_prepared(ws, P, nt, s);
-      if (!st) st = zero_state(nshots, shots, s);
-      if (!st) st = issue_steps(ws, P, R, t, 1, s);  // warm-up
-      if (st) {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        return st;
-      }
-      cudaEventRecord(a, s);
-      st = issue_steps(ws, P, R, t, trial, s);
-      cudaEventRecord(b, s);
-      if (st || cudaEventSynchronize(b)) {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        return st ? st : fail(FD_ERR_CUDA, "autotune timing failed");
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (ms < best_ms) {
-        best_ms = ms;
-        *best = t;
-      }
+  fd_status st = FD_OK;
+  for (int i = 0; i < kNumShapes && !st; ++i) {
+    TileShape t = kShapes[i];
+    Prepared P;
+    st = prepare(nshots, shots, t, P);
+    if (!st) st = upload_prepared(ws, P, s);
+    if (!st) st = zero_state(nshots, shots, s);
+    if (!st) st = issue_steps(ws, P, R, t, 1, s);  // warm-up
+    if (st) break;
+    cudaEventRecord(a, s);
+    st = issue_steps(ws, P, R, t, trial, s);
+    cudaEventRecord(b, s);
+    if (st) break;
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      st = fail(FD_ERR_CUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = t;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return FD_OK;
+  return st;
 }
 
 }  // namespace
@@ -269,6 +213,7 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
   clear_error();
   if (nshots < 1 || !shots) return fail(FD_ERR_ARG, "no shots");
   fd_grid g0 = shots[0].grid;
+  if (!g0) return fail(FD_ERR_ARG, "shot 0 has no grid");
   for (int i = 0; i < nshots; ++i) {
     fd_grid g = shots[i].grid;
     if (!g) return fail(FD_ERR_ARG, "shot %d has no grid", i);
@@ -302,27 +247,25 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
     if ((st = autotune(ws, nshots, shots, R, nt, s, &t))) return st;
     g_tuned[key] = t;
     save_cache_entry(key, t);
-    ws.graph_valid = false;
   }
 
   Prepared P;
   if ((st = prepare(nshots, shots, t, P))) return st;
-  if ((st = upload_prepared(ws, P, nt, s))) return st;
+  if ((st = upload_prepared(ws, P, s))) return st;
   if ((st = zero_state(nshots, shots, s))) return st;
 
   const bool use_graph = (flags & FD_BATCH_GRAPH) && nt >= 2;
-  // the graph depends on the launch shape and the workspace pointers only;
-  // descriptors live in device memory and were just refreshed
-  std::vector<char> key_bytes(sizeof(TileShape) + 4 * sizeof(int) + 3 * sizeof(void*));
+  // the captured launches depend on the shape, sizes and workspace address;
+  // the descriptors are re-uploaded before each replay
+  std::vector<char> key_bytes(sizeof(TileShape) + 4 * sizeof(int) + sizeof(void*));
   {
     char* q = key_bytes.data();
     memcpy(q, &t, sizeof(t));
     q += sizeof(t);
-    int ints[4] = {R, nt, P.nwork, P.grid};
+    int ints[4] = {R, nt, P.nshots, P.ctas};
     memcpy(q, ints, sizeof(ints));
     q += sizeof(ints);
-    void* ptrs[3] = {ws.shots.p, ws.work.p, ws.counters.p};
-    memcpy(q, ptrs, sizeof(ptrs));
+    memcpy(q, &ws.desc.p, sizeof(void*));
   }
   if (g0->profiling) cudaEventRecord(g0->ev0, s);
   cudaError_t e;
@@ -365,13 +308,14 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
   for (int i = 0; i < nshots; ++i) {
     fd_grid g = shots[i].grid;
     g->F.cur = nt & 1;
-    // every grid's error word is written on stream s
-    std::swap(g->stream, s);
+    // every grid's error word and receivers were written on stream s
+    cudaStream_t own = g->stream;
+    g->stream = s;
     st = check_device_error(g);
     const int nrec = shots[i].rec ? shots[i].rec->n : 0;
     if (!st && nrec) st = check_finite(g, P.drec[i], size_t(nt) * nrec);
     if (!st && nrec) st = finish_out(g, shots[i].rec_out, P.drec[i], size_t(nt) * nrec);
-    std::swap(g->stream, s);
+    g->stream = own;
     if (st) return st;
   }
   e = cudaStreamSynchronize(s);

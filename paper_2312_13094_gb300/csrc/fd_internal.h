@@ -39,7 +39,7 @@ struct StepArgs {
   int32_t Nx, Ny, Nz;      // padded extents
   int32_t pitch;           // floats per row of every device array
   int32_t nbl, nx, ny, nz; // layer width and physical extents
-  int32_t tiles_x, tiles_y, zsplit, zlen;
+  int32_t tiles_x, tiles_y;
   float bscale;            // gamma_max * dt / 2 / nbl^2
   float c[kMaxR + 1];      // second-derivative weights c_0..c_R
   float* out;              // u^{n+1}: the u^{n-1} buffer, updated in place
@@ -62,33 +62,38 @@ struct StepArgs {
   int32_t debug_skip_plane;  // test hook: never issue this plane's load (-1)
 };
 
-// One shot of a batched launch (device memory, 64-byte aligned for the maps).
-struct BatchShot {
+// One grid of a sweep launch (device memory): its tensor maps, constants and
+// buffers.  Step-dependent values come from StepOverride.
+struct ShotDesc {
   CUtensorMap halo[2];  // u^n with halo, per buffer
   CUtensorMap tile[2];  // u^{n-1} tiles, per buffer
-  CUtensorMap A;
-  StepArgs args;        // per-shot constants; rows are set per launch
+  CUtensorMap A;        // model term tiles
+  CUtensorMap C;        // per-cell weight tiles (fields stacked along z) or A
+  StepArgs args;
   float* u[2];
+};
+
+// Per-launch values of a sweep: buffer parity, table rows, imaging fields.
+struct StepOverride {
+  int cur;            // u[cur] holds u^n
+  int inj_row;
+  int rec_row;
+  int pad_;
+  float* e_out;
+  const float* e_in;
 };
 
 struct TileShape {
   int tx, ty, pf;   // threads in x (4 points each), rows, prefetch depth
-  int zsplit;       // z chunks per column
+  int ctas;         // persistent CTAs per sweep (0: resident CTAs per SM x SMs)
 };
 
 // Per-radius launchers, specialised in fd_step_r<R>.cu.
 template <int R>
-cudaError_t launch_step_r(const TileShape& t, int mode, const CUtensorMap& halo,
-                          const CUtensorMap& tile_prev, const CUtensorMap& tileA,
-                          const CUtensorMap& tileC, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_r(const TileShape& t, int mode, const ShotDesc* shots,
+                           const long long* prefix, int nshots, const StepOverride& ov,
+                           int grid, cudaStream_t s);
 template <int R>
-cudaError_t launch_batch_r(const TileShape& t, const BatchShot* shots, const int4* work,
-                           int nwork, int* counter, int step, int grid, cudaStream_t s);
-template <int R>
-int batch_blocks_per_sm_r(const TileShape& t);
-template <int R>
-size_t smem_r(const TileShape& t);
-template <int R>
-int regs_r(const TileShape& t);
+int sweep_blocks_per_sm_r(const TileShape& t, int mode);
 
 }  // namespace fd

@@ -153,39 +153,46 @@ fd_status build_maps(fd_grid g) {
 // --------------------------------------------------------------------------
 // dispatch over radius
 // --------------------------------------------------------------------------
-cudaError_t launch_step(int R, const TileShape& t, int mode, const CUtensorMap& h,
-                        const CUtensorMap& p, const CUtensorMap& A, const CUtensorMap& C,
-                        const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_sweep(int R, const TileShape& t, int mode, const ShotDesc* shots,
+                         const long long* prefix, int nshots, const StepOverride& ov, int grid,
+                         cudaStream_t s) {
   count_launch();
   switch (R) {
-    case 1: return launch_step_r<1>(t, mode, h, p, A, C, a, s);
-    case 2: return launch_step_r<2>(t, mode, h, p, A, C, a, s);
-    case 3: return launch_step_r<3>(t, mode, h, p, A, C, a, s);
-    case 4: return launch_step_r<4>(t, mode, h, p, A, C, a, s);
-    case 5: return launch_step_r<5>(t, mode, h, p, A, C, a, s);
-    case 6: return launch_step_r<6>(t, mode, h, p, A, C, a, s);
-    case 7: return launch_step_r<7>(t, mode, h, p, A, C, a, s);
-    case 8: return launch_step_r<8>(t, mode, h, p, A, C, a, s);
+    case 1: return launch_sweep_r<1>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 2: return launch_sweep_r<2>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 3: return launch_sweep_r<3>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 4: return launch_sweep_r<4>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 5: return launch_sweep_r<5>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 6: return launch_sweep_r<6>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 7: return launch_sweep_r<7>(t, mode, shots, prefix, nshots, ov, grid, s);
+    case 8: return launch_sweep_r<8>(t, mode, shots, prefix, nshots, ov, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-size_t step_smem(int R, const TileShape& t) {
+// Persistent CTAs of a sweep: the explicit count of the tile shape, else the
+// CTAs that fit on all SMs at once.
+int sweep_ctas(int R, const TileShape& t, int mode) {
+  if (t.ctas > 0) return t.ctas;
+  int per = 0;
   switch (R) {
-    case 1: return smem_r<1>(t);
-    case 2: return smem_r<2>(t);
-    case 3: return smem_r<3>(t);
-    case 4: return smem_r<4>(t);
-    case 5: return smem_r<5>(t);
-    case 6: return smem_r<6>(t);
-    case 7: return smem_r<7>(t);
-    case 8: return smem_r<8>(t);
+    case 1: per = sweep_blocks_per_sm_r<1>(t, mode); break;
+    case 2: per = sweep_blocks_per_sm_r<2>(t, mode); break;
+    case 3: per = sweep_blocks_per_sm_r<3>(t, mode); break;
+    case 4: per = sweep_blocks_per_sm_r<4>(t, mode); break;
+    case 5: per = sweep_blocks_per_sm_r<5>(t, mode); break;
+    case 6: per = sweep_blocks_per_sm_r<6>(t, mode); break;
+    case 7: per = sweep_blocks_per_sm_r<7>(t, mode); break;
+    case 8: per = sweep_blocks_per_sm_r<8>(t, mode); break;
   }
-  return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, per) * std::max(1, sms);
 }
 
 const TileShape kShapes[kNumShapes] = {
-    {16, 16, 2, 1}, {32, 8, 2, 1}, {8, 32, 2, 1}, {16, 8, 3, 1}};
+    {16, 16, 2, 0}, {32, 8, 2, 0}, {8, 32, 2, 0}, {16, 8, 3, 0}};
 
 // Default tile: 64x16 for the narrow stencils, 128x8 when the halo is wide.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
@@ -202,8 +209,6 @@ void set_shape(fd_grid g, TileShape t) {
   g->shape = t;
   g->tiles_x = (g->Nx + bx - 1) / bx;
   g->tiles_y = (g->Ny + by - 1) / by;
-  if (t.zsplit < 1) g->shape.zsplit = 1;
-  g->zlen = (g->Nz + g->shape.zsplit - 1) / g->shape.zsplit;
   g->graph_valid = false;
 }
 
@@ -415,8 +420,6 @@ StepArgs base_args(fd_grid g) {
   a.nz = g->d.nz;
   a.tiles_x = g->tiles_x;
   a.tiles_y = g->tiles_y;
-  a.zsplit = g->shape.zsplit;
-  a.zlen = g->zlen;
   a.bscale = g->bscale;
   for (int j = 0; j <= kMaxR; ++j) a.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
   a.err = g->d_err;
@@ -425,26 +428,81 @@ StepArgs base_args(fd_grid g) {
   return a;
 }
 
+// Host image of the sweep descriptor of one run (grid, field pair, tables).
+void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d) {
+  memset(d, 0, sizeof(*d));
+  Fields& F = *rs.f;
+  for (int b = 0; b < 2; ++b) {
+    d->halo[b] = F.halo[b];
+    d->tile[b] = F.tile[b];
+    d->u[b] = F.u[b];
+  }
+  d->A = g->mapA;
+  d->C = g->coef ? g->mapC : g->mapA;
+  d->args = base_args(g);
+  if (rs.inj_val) {
+    d->args.inj_start = rs.inj_start;
+    d->args.inj = rs.inj;
+    d->args.inj_val = rs.inj_val;
+    d->args.inj_ncol = rs.inj_ncol;
+  }
+  if (rs.rec_out) {
+    d->args.rec_start = rs.rec_start;
+    d->args.recs = rs.recs;
+    d->args.rec_out = rs.rec_out;
+    d->args.rec_ncol = rs.rec_ncol;
+  }
+  d->args.grad = rs.grad;
+  d->args.inv_dt2 = float(1.0 / (g->d.dt * g->d.dt));
+  d->args.out = nullptr;
+}
+
 fd_status run_steps(fd_grid g, const RunSpec& rs) {
   if (rs.nsteps <= 0) return FD_OK;
   cudaError_t e;
   Fields& F = *rs.f;
+  const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
+  const int G = sweep_ctas(g->R, g->shape, mode);
+  // descriptor + unit prefix, refreshed before every run (stream ordered),
+  // so a captured graph stays valid when tables or caller arrays move
+  struct {
+    ShotDesc d;
+    long long prefix[2];
+  } host;
+  fill_desc(g, rs, &host.d);
+  host.d.args.debug_skip_plane = g->debug_skip_plane;
+  host.prefix[0] = 0;
+  host.prefix[1] = (long long)g->tiles_x * g->tiles_y * g->Nz;
+  const int slot = (&F == &g->Z) ? 1 : 0;
+  e = g->desc.ensure(2 * sizeof(host));
+  if (e) return cuda_fail(e, "descriptor allocation");
+  char* dslot = static_cast<char*>(g->desc.p) + slot * sizeof(host);
+  e = cudaMemcpyAsync(dslot, &host, sizeof(host), cudaMemcpyHostToDevice, g->stream);
+  if (e) return cuda_fail(e, "descriptor upload");
+  const ShotDesc* dshot = reinterpret_cast<const ShotDesc*>(dslot);
+  const long long* dprefix = reinterpret_cast<const long long*>(dslot + sizeof(ShotDesc));
+
   const bool use_graph = rs.allow_graph && rs.nsteps >= 2 && !g->no_graph;
   GraphKey key;
   memset(&key, 0, sizeof(key));
-  key.spec = rs;
+  key.mode = mode;
+  key.nsteps = rs.nsteps;
   key.cur = F.cur;
+  key.slot = slot;
+  key.inj_row0 = rs.inj_row0;
+  key.inj_row_step = rs.inj_row_step;
+  key.rec_row0 = rs.rec_row0;
+  key.rec_row_step = rs.rec_row_step;
+  key.e_base = rs.e_base;
+  key.e_idx0 = rs.e_idx0;
+  key.e_idx_step = rs.e_idx_step;
   key.shape = g->shape;
-  key.skip = g->debug_skip_plane + (g->percell ? 1 << 20 : 0);
-  key.bscale = g->bscale;
+  key.ctas = G;
+  key.desc = dslot;
   const bool reuse = use_graph && g->graph_valid && memcmp(&key, &g->gkey, sizeof(key)) == 0;
   if (g->profiling) cudaEventRecord(g->ev0, g->stream);
-  if (reuse) {
-    e = cudaGraphLaunch(g->gexec, g->stream);
-    if (e) return cuda_fail(e, "graph launch");
-    count_launch(rs.nsteps);
-    F.cur = (F.cur + rs.nsteps) & 1;
-  } else {
+  const int cur0 = F.cur;
+  if (!reuse) {
     if (use_graph) {
       if (g->graph_valid) {
         cudaGraphExecDestroy(g->gexec);
@@ -453,49 +511,34 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed);
       if (e) return cuda_fail(e, "stream capture");
     }
-    const int cur0 = F.cur;
-    long long before = g_launches.load();
+    const long long before = g_launches.load();
     for (int t = 0; t < rs.nsteps; ++t) {
-      const int cur = (cur0 + t) & 1, prev = cur ^ 1;
-      StepArgs a = base_args(g);
-      a.out = F.u[prev];
-      a.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
-      if (rs.inj_val) {
-        a.inj_start = rs.inj_start;
-        a.inj = rs.inj;
-        a.inj_val = rs.inj_val;
-        a.inj_ncol = rs.inj_ncol;
-        a.inj_row = rs.inj_row0 + rs.inj_row_step * t;
+      StepOverride ov;
+      memset(&ov, 0, sizeof(ov));
+      ov.cur = (cur0 + t) & 1;
+      ov.inj_row = rs.inj_row0 + rs.inj_row_step * t;
+      ov.rec_row = rs.rec_row0 + rs.rec_row_step * t;
+      if (mode == kModeStoreE) ov.e_out = rs.e_base + size_t(t) * g->ncell;
+      if (mode == kModeAdjoint)
+        ov.e_in = rs.e_base + size_t(rs.e_idx0 + rs.e_idx_step * t) * g->ncell;
+      if (t == 1 && g->debug_skip_plane >= 0) {
+        // the test hook applies to the first step only
+        host.d.args.debug_skip_plane = -1;
+        e = cudaMemcpyAsync(dslot, &host, sizeof(host), cudaMemcpyHostToDevice, g->stream);
+        if (e) return cuda_fail(e, "descriptor upload");
       }
-      if (rs.rec_out) {
-        a.rec_start = rs.rec_start;
-        a.recs = rs.recs;
-        a.rec_out = rs.rec_out;
-        a.rec_ncol = rs.rec_ncol;
-        a.rec_row = rs.rec_row0 + rs.rec_row_step * t;
-      }
-      if (rs.mode == kModeStoreE) a.e_out = rs.e_base + size_t(t) * g->ncell;
-      if (rs.mode == kModeAdjoint) {
-        a.e_in = rs.e_base + size_t(rs.e_idx0 + rs.e_idx_step * t) * g->ncell;
-        a.grad = rs.grad;
-        a.inv_dt2 = float(1.0 / (g->d.dt * g->d.dt));
-      }
-      const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
-      e = launch_step(g->R, g->shape, mode, F.halo[cur], F.tile[prev], g->mapA,
-                      g->coef ? g->mapC : g->mapA, a, g->stream);
+      e = launch_sweep(g->R, g->shape, mode, dshot, dprefix, 1, ov, G, g->stream);
       if (e) {
         if (use_graph) {
-          cudaGraph_t dummy;
+          cudaGraph_t dummy = nullptr;
           cudaStreamEndCapture(g->stream, &dummy);
           if (dummy) cudaGraphDestroy(dummy);
         }
         return cuda_fail(e, "step launch");
       }
     }
-    F.cur = (cur0 + rs.nsteps) & 1;
     if (use_graph) {
-      // count the graph's launches when it runs, not at capture
-      g_launches.store(before);
+      g_launches.store(before);  // counted when the graph runs
       cudaGraph_t graph;
       e = cudaStreamEndCapture(g->stream, &graph);
       if (e) return cuda_fail(e, "end capture");
@@ -503,13 +546,15 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       cudaGraphDestroy(graph);
       if (e) return cuda_fail(e, "graph instantiate");
       g->graph_valid = true;
-      key.cur = cur0;
       g->gkey = key;
-      e = cudaGraphLaunch(g->gexec, g->stream);
-      if (e) return cuda_fail(e, "graph launch");
-      count_launch(rs.nsteps);
     }
   }
+  if (use_graph) {
+    e = cudaGraphLaunch(g->gexec, g->stream);
+    if (e) return cuda_fail(e, "graph launch");
+    count_launch(rs.nsteps);
+  }
+  F.cur = (cur0 + rs.nsteps) & 1;
   if (g->profiling) {
     cudaEventRecord(g->ev1, g->stream);
     e = cudaEventSynchronize(g->ev1);
@@ -683,7 +728,7 @@ fd_status fd_destroy_grid(fd_grid g) {
                     &g->tab_adj.inj_start, &g->tab_adj.inj, &g->tab_adj.rec_start,
                     &g->tab_adj.recs,
                     &g->stage_val, &g->stage_rec, &g->stage_aux, &g->ckpt, &g->ebuf,
-                    &g->gpad, &g->resid, &g->recbuf})
+                    &g->gpad, &g->resid, &g->recbuf, &g->desc})
     b->release();
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
@@ -857,7 +902,7 @@ fd_status fd_get_info(fd_grid g, fd_grid_info* info) {
   info->pitch = g->pitch;
   info->tile_x = 4 * g->shape.tx;
   info->tile_y = g->shape.ty;
-  info->zsplit = g->shape.zsplit;
+  info->ctas = sweep_ctas(g->R, g->shape, g->percell ? int(kModePerCell) : int(kModeForward));
   info->v_max = g->vmax;
   info->cfl_limit = g->cfl;
   info->launches = g_launches.load();
@@ -925,15 +970,15 @@ fd_status fd_set_learned_coefficients(fd_grid g, fd_mlp net, double f_hz) {
   return FD_OK;
 }
 
-fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t zsplit) {
+fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t ctas) {
   clear_error();
   if (!g) return fail(FD_ERR_ARG, "null grid");
-  if (zsplit < 1 || zsplit > g->Nz) return fail(FD_ERR_ARG, "zsplit must be in 1..nz_pad");
+  if (ctas < 0) return fail(FD_ERR_ARG, "ctas must be >= 0");
   for (int i = 0; i < kNumShapes; ++i) {
     if (4 * kShapes[i].tx == tile_x && kShapes[i].ty == tile_y) {
       cudaSetDevice(g->d.device);
       TileShape t = kShapes[i];
-      t.zsplit = zsplit;
+      t.ctas = ctas;
       set_shape(g, t);
       return build_maps(g);
     }

@@ -51,12 +51,16 @@ struct RunSpec {
   float* grad;
 };
 
+// Everything that fixes the launches of a captured run (the descriptor
+// contents are refreshed before each replay and are not part of it).
 struct GraphKey {
-  RunSpec spec;
-  int cur;
+  int mode, nsteps, cur, slot;
+  int inj_row0, inj_row_step, rec_row0, rec_row_step;
+  float* e_base;
+  int e_idx0, e_idx_step;
   TileShape shape;
-  int skip;
-  float bscale;
+  int ctas;
+  void* desc;
 };
 
 constexpr int kNumShapes = 4;
@@ -85,10 +89,11 @@ struct fd_grid_s {
   double c[fd::kMaxR + 1] = {};
   double cfl = 0.0;
   fd::TileShape shape = {};
-  int tiles_x = 0, tiles_y = 0, zlen = 0;
+  int tiles_x = 0, tiles_y = 0;
   fd::Tables tab, tab_adj;
   fd::DevBuf stage_val, stage_rec, stage_aux, recbuf;
   fd::DevBuf ckpt, ebuf, gpad, resid;
+  fd::DevBuf desc;  // sweep descriptors (forward and adjoint slots)
   int32_t* d_err = nullptr;  // [0] wait-timeout word, [1] finite count, [4..6] scratch
   long long spin_limit = 0;
   int debug_skip_plane = -1;
@@ -113,10 +118,11 @@ fd_status build_maps(fd_grid g);
 fd_status build_field_maps(fd_grid g, Fields& f);
 void set_shape(fd_grid g, TileShape t);
 TileShape default_shape(int R, int Nx, int Ny, int Nz);
-size_t step_smem(int R, const TileShape& t);
-cudaError_t launch_step(int R, const TileShape& t, int mode, const CUtensorMap& h,
-                        const CUtensorMap& p, const CUtensorMap& A, const CUtensorMap& C,
-                        const StepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep(int R, const TileShape& t, int mode, const ShotDesc* shots,
+                         const long long* prefix, int nshots, const StepOverride& ov, int grid,
+                         cudaStream_t s);
+int sweep_ctas(int R, const TileShape& t, int mode);
+void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d);
 StepArgs base_args(fd_grid g);
 fd_status upload_tables(fd_grid g, const fd_points* src, double src_scale,
                         const fd_points* rec, Tables& t);

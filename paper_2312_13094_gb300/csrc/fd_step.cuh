@@ -52,6 +52,23 @@ struct Cfg {
   static_assert(W <= 256 && H <= 256, "TMA box too large");
 };
 
+// Prefetch depth of a tile shape: the deepest ring (1..6 planes beyond the
+// R+1 in use) whose shared memory still lets the CTAs that the register file
+// admits be resident together (two CTAs of 256 threads or four of 128).
+template <int R, int TX, int TY, int NC>
+constexpr int auto_pf() {
+  const uint32_t budget = (TX * TY >= 256) ? 110u * 1024u : 54u * 1024u;
+  const int rx = ((R + 3) / 4) * 4;
+  const uint32_t up = ((4 * TX + 2 * rx) * (TY + 2 * R) * 4 + 127) / 128 * 128;
+  const uint32_t tp = (4 * TX * TY * 4 + 127) / 128 * 128;
+  for (int pf = 6; pf > 1; --pf) {
+    const uint32_t smem = (R + 1 + pf) * up + (pf + 1) * (2 + NC) * tp +
+                          (R + 1 + pf + pf + 1) * 8 + 128;
+    if (smem <= budget) return pf;
+  }
+  return 1;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -119,15 +136,15 @@ __device__ __forceinline__ float lane(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// One CTA: the xy tile (tile_x, tile_y), z chunk zc.  All threads of the CTA
-// must call this with the same arguments.
+// One CTA: the xy tile (tile_x, tile_y), output planes [zbeg, zend).  All
+// threads of the CTA must call this with the same arguments.
 template <int R, int TX, int TY, int PF, int MODE>
 __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            const CUtensorMap* tm_prev,
                                            const CUtensorMap* tm_A,
                                            const CUtensorMap* tm_C,
                                            const StepArgs& a, float* __restrict__ out,
-                                           int tile_x, int tile_y, int zc,
+                                           int tile_x, int tile_y, int zbeg, int zend,
                                            unsigned char* smem) {
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
@@ -136,8 +153,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const int ty = tid / TX;
   const int x0 = tile_x * C::BX;
   const int y0 = tile_y * C::BY;
-  const int zbeg = zc * a.zlen;
-  const int zend = min(a.Nz, zbeg + a.zlen);
   if (zbeg >= zend) return;
   const int zl = zend - zbeg;
   const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
@@ -326,8 +341,11 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       for (int l = 0; l < 4; ++l) {
         const float b = a.bscale * (dxx[l] + dzz);
         const float uc = lane(q[R], l);
-        const float e = lane(Av, l) * (lap[l] + src[l]);
-        float t = fmaf(-(1.0f - b), lane(up, l), 2.0f * uc) + e;
+        // the same explicit roundings in every mode, so that a recomputed
+        // segment reproduces the stored states bit for bit
+        const float ls = __fadd_rn(lap[l], src[l]);
+        const float e = __fmul_rn(lane(Av, l), ls);
+        float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
         if (b != 0.0f) t = t / (1.0f + b);
         res[l] = (gx + l < a.Nx) ? t : 0.0f;
         ev[l] = (gx + l < a.Nx) ? e : 0.0f;
@@ -399,50 +417,47 @@ fail:
   }
 }
 
+// Persistent sweep over every (tile, plane) work unit of one or more grids.
+// The units of shot s are numbered tile-major (unit = tile * Nz + z) after the
+// units of shots 0..s-1; CTA c of G takes the contiguous share
+// [c*total/G, (c+1)*total/G), cut into per-tile z segments.  With G equal to
+// the number of resident CTAs every SM streams the same number of planes and
+// no CTA waits for a second wave.
 template <int R, int TX, int TY, int PF, int MODE>
 __global__ void __launch_bounds__(TX* TY, 2)
-    step_kernel(const __grid_constant__ CUtensorMap halo,
-                const __grid_constant__ CUtensorMap tprev,
-                const __grid_constant__ CUtensorMap tA,
-                const __grid_constant__ CUtensorMap tC,
-                const __grid_constant__ StepArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-  run_column<R, TX, TY, PF, MODE>(&halo, &tprev, &tA, &tC, a, a.out, blockIdx.x,
-                                  blockIdx.y, blockIdx.z, smem);
-}
-
-// Many shots in one persistent launch: CTAs pull {shot, tile, z chunk} items
-// (sorted longest first) from an atomic counter; each item is one column of
-// run_column on that shot's buffers.  Time step t selects the buffer parity
-// and the wavelet / receiver rows.
-template <int R, int TX, int TY, int PF>
-__global__ void __launch_bounds__(TX* TY, 2)
-    batch_kernel(const BatchShot* __restrict__ shots, const int4* __restrict__ work,
-                 int nwork, int* __restrict__ counter, int t) {
+    sweep_kernel(const ShotDesc* __restrict__ shots, const long long* __restrict__ prefix,
+                 int nshots, const __grid_constant__ StepOverride ov) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ StepArgs sa;
-  __shared__ int item;
-  const int cur = t & 1;
-  for (;;) {
-    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = item;
-    if (it >= nwork) break;
-    const int4 w = work[it];
-    const BatchShot* S = shots + w.x;
+  const long long total = prefix[nshots];
+  const long long lo = total * blockIdx.x / gridDim.x;
+  const long long hi = total * (blockIdx.x + 1) / gridDim.x;
+  const int cur = ov.cur;
+  int s = 0;
+  for (long long pos = lo; pos < hi;) {
+    while (pos >= prefix[s + 1]) ++s;
+    const ShotDesc* S = shots + s;
+    const long long local = pos - prefix[s];
+    const int Nz = S->args.Nz;
+    const int tile = static_cast<int>(local / Nz);
+    const int zb = static_cast<int>(local % Nz);
+    const long long left = hi - pos;
+    const int ze = left < Nz - zb ? zb + static_cast<int>(left) : Nz;
     if (threadIdx.x == 0) {
       sa = S->args;
-      sa.inj_row = t;
-      sa.rec_row = t;
+      sa.inj_row = ov.inj_row;
+      sa.rec_row = ov.rec_row;
+      sa.e_out = ov.e_out;
+      sa.e_in = ov.e_in;
     }
     __syncthreads();
-    run_column<R, TX, TY, PF, kModeForward>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->A, sa,
-                                            S->u[cur ^ 1], w.y, w.z, w.w, smem);
+    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->C, sa,
+                                    S->u[cur ^ 1], tile % sa.tiles_x, tile / sa.tiles_x, zb,
+                                    ze, smem);
     __syncthreads();
+    pos += ze - zb;
   }
 }
 
