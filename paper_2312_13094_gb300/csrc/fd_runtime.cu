@@ -462,7 +462,11 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   cudaError_t e;
   Fields& F = *rs.f;
   const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
-  const int G = sweep_ctas(g->R, g->shape, mode);
+  // one whole column per CTA when all columns fit on the GPU at once: every
+  // CTA then walks z in step with its neighbours, which share halos in L2;
+  // otherwise equal contiguous shares of the (tile, plane) units
+  int G = sweep_ctas(g->R, g->shape, mode);
+  if (g->shape.ctas == 0) G = std::min<long long>(G, (long long)g->tiles_x * g->tiles_y);
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
   struct {

@@ -53,11 +53,11 @@ struct Cfg {
 };
 
 // Prefetch depth of a tile shape: the deepest ring (1..6 planes beyond the
-// R+1 in use) whose shared memory still lets the CTAs that the register file
-// admits be resident together (two CTAs of 256 threads or four of 128).
+// R+1 in use) whose shared memory still lets the CTAs that the launch bounds
+// admit be resident together (three CTAs of 256 threads or six of 128).
 template <int R, int TX, int TY, int NC>
 constexpr int auto_pf() {
-  const uint32_t budget = (TX * TY >= 256) ? 110u * 1024u : 54u * 1024u;
+  const uint32_t budget = (TX * TY >= 256) ? 72u * 1024u : 36u * 1024u;
   const int rx = ((R + 3) / 4) * 4;
   const uint32_t up = ((4 * TX + 2 * rx) * (TY + 2 * R) * 4 + 127) / 128 * 128;
   const uint32_t tp = (4 * TX * TY * 4 + 127) / 128 * 128;
@@ -346,7 +346,9 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         const float ls = __fadd_rn(lap[l], src[l]);
         const float e = __fmul_rn(lane(Av, l), ls);
         float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
-        if (b != 0.0f) t = t / (1.0f + b);
+        // inside the layer divide by 1+b (fast reciprocal; select, no branch)
+        const float td = __fdividef(t, 1.0f + b);
+        t = (b != 0.0f) ? td : t;
         res[l] = (gx + l < a.Nx) ? t : 0.0f;
         ev[l] = (gx + l < a.Nx) ? e : 0.0f;
       }
@@ -424,7 +426,7 @@ fail:
 // the number of resident CTAs every SM streams the same number of planes and
 // no CTA waits for a second wave.
 template <int R, int TX, int TY, int PF, int MODE>
-__global__ void __launch_bounds__(TX* TY, 2)
+__global__ void __launch_bounds__(TX* TY, (TX * TY >= 256) ? 3 : 6)
     sweep_kernel(const ShotDesc* __restrict__ shots, const long long* __restrict__ prefix,
                  int nshots, const __grid_constant__ StepOverride ov) {
   extern __shared__ unsigned char smem_raw[];

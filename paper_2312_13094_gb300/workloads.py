@@ -189,7 +189,7 @@ def adjoint_256(n: int = 256, nt: int = 500, nbl: int = 20, anomaly=True):
     r2 = ((ax[None, None, :] - c) ** 2 + (ax[None, :, None] - c) ** 2
           + (ax[:, None, None] - c) ** 2)
     shape = np.exp(-r2 / (2.0 * (n / 12.8) ** 2))
-    v = (2.0 + (0.2 * shape if anomaly else 0.0)).astype(np.float32)
+    v = (2.0 + (0.2 * shape if anomaly else np.zeros_like(shape))).astype(np.float32)
     src = np.array([[n / 2 * h, n / 2 * h, n / 4 * h]])
     g = np.linspace(0.0, (n - 1) * h, 32)
     gx, gy = np.meshgrid(g, g, indexing="xy")
