@@ -238,6 +238,30 @@ fd_status fd_mlp_make_samples(int32_t n, const float* prev, const float* cur, co
                               const float* vel, double h, double dt, double f_hz, double scale,
                               float* out);
 
+/* Forward modelling for callers that cannot allocate device memory (for
+ * example while another framework owns the memory pool and forbids new
+ * cudaMalloc calls, or when the device footprint must stay fixed).  It does
+ * what fd_create_grid + fd_set_model + fd_forward + fd_destroy_grid do, but
+ * every buffer it needs (wavefields, model term, tables, descriptors) lives in
+ * one static device array of FD_NOALLOC_MAX_BYTES that the library keeps on
+ * each GPU that loads it, and it calls no allocating routine.  The paper has
+ * no counterpart of this entry point.
+ *   desc     as for fd_create_grid (desc->stream may be NULL: legacy stream);
+ *            no graph, events or stream are created
+ *   model    DEVICE array, nz*ny*nx values of `kind` (FD_MODEL_*)
+ *   wavelet  DEVICE [nt][src->n];  rec_out DEVICE [nt][rec->n]
+ * Errors: FD_ERR_ARG when the padded grid and tables do not fit in the array
+ * (the message gives the bytes needed) or an array is host memory; otherwise
+ * as fd_set_model and fd_forward.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make it before any stream
+ * capture.  All calls share the array and leave the last call's contents in
+ * it; calls that overlap on the GPU race and must be serialised by the
+ * caller. */
+#define FD_NOALLOC_MAX_BYTES (32 * 1024 * 1024)
+fd_status fd_forward_noalloc(const fd_grid_desc* desc, const float* model, int32_t kind,
+                             const fd_points* src, const float* wavelet,
+                             const fd_points* rec, float* rec_out);
+
 /* Diagnostics. */
 fd_status fd_get_info(fd_grid grid, fd_grid_info* info);
 /* When enabled, fd_forward / fd_propagate / fd_batch_forward record CUDA

@@ -95,6 +95,8 @@ _SIGS = {
     "fd_sample_stencil": (_S, [_G, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "fd_mlp_make_samples": (_S, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
+    "fd_forward_noalloc": (_S, [ctypes.POINTER(fd_grid_desc), _P, ctypes.c_int32, _PTS, _P,
+                                _PTS, _P]),
     "fd_set_tile": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_debug": (_S, [_G, ctypes.c_int32, ctypes.c_int64]),
     "fd_get_info": (_S, [_G, ctypes.POINTER(fd_grid_info)]),
