@@ -77,6 +77,8 @@ struct Prepared {
   std::vector<float*> drec;
   int nshots = 0;
   int ctas = 0;
+  float c[kMaxR + 1] = {};  // stencil weights (the same for every shot)
+  long long spin_limit = 0;
 };
 
 // Puts every shot on tile shape t and builds the descriptors and the unit
@@ -129,6 +131,9 @@ fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared
     prefix[i + 1] = prefix[i] + (long long)g->tiles_x * g->tiles_y * g->Nz;
   }
   P.ctas = sweep_ctas(R, t, kModeForward);
+  fd_grid g0 = shots[0].grid;
+  for (int j = 0; j <= kMaxR; ++j) P.c[j] = j <= R ? float(g0->c[j]) : 0.0f;
+  P.spin_limit = g0->spin_limit;
   return FD_OK;
 }
 
@@ -165,6 +170,9 @@ fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileSh
     ov.cur = step & 1;
     ov.inj_row = step;
     ov.rec_row = step;
+    ov.spin_limit = P.spin_limit;
+    ov.debug_skip_plane = -1;
+    for (int j = 0; j <= kMaxR; ++j) ov.c[j] = P.c[j];
     cudaError_t e = launch_sweep(R, t, kModeForward, d, prefix, P.nshots, ov, P.ctas, s);
     if (e) return cuda_fail(e, "batch launch");
   }
@@ -219,6 +227,8 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
     if (!g) return fail(FD_ERR_ARG, "shot %d has no grid", i);
     if (!g->model_set) return fail(FD_ERR_STATE, "shot %d has no model", i);
     if (g->percell) return fail(FD_ERR_STATE, "shot %d uses per-cell weights", i);
+    for (int j = 0; j <= g->R && j <= g0->R; ++j)
+      if (g->c[j] != g0->c[j]) return fail(FD_ERR_ARG, "shots must share stencil weights");
     if (g->d.device != g0->d.device || g->R != g0->R || g->d.nt != g0->d.nt)
       return fail(FD_ERR_ARG, "shots must share device, space order and nt");
     for (int j = 0; j < i; ++j)

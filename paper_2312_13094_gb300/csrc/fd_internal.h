@@ -78,9 +78,11 @@ struct StepOverride {
   int cur;            // u[cur] holds u^n
   int inj_row;
   int rec_row;
-  int pad_;
+  int debug_skip_plane;      // test hook: never issue this plane's load (-1)
   float* e_out;
   const float* e_in;
+  long long spin_limit;      // clock cycles before a wait gives up
+  float c[kMaxR + 1];        // stencil weights shared by every shot of the launch
 };
 
 struct TileShape {

@@ -462,11 +462,13 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   cudaError_t e;
   Fields& F = *rs.f;
   const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
-  // one whole column per CTA when all columns fit on the GPU at once: every
-  // CTA then walks z in step with its neighbours, which share halos in L2;
-  // otherwise equal contiguous shares of the (tile, plane) units
+  // one whole column per CTA when the columns fill at least half of the
+  // resident slots: every CTA then walks z in step with its neighbours, which
+  // share halos in L2; otherwise equal contiguous shares of all the
+  // (tile, plane) units over every resident slot
   int G = sweep_ctas(g->R, g->shape, mode);
-  if (g->shape.ctas == 0) G = std::min<long long>(G, (long long)g->tiles_x * g->tiles_y);
+  const long long T = (long long)g->tiles_x * g->tiles_y;
+  if (g->shape.ctas == 0 && T < G && 2 * T >= G) G = int(T);
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
   struct {
@@ -474,7 +476,6 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
     long long prefix[2];
   } host;
   fill_desc(g, rs, &host.d);
-  host.d.args.debug_skip_plane = g->debug_skip_plane;
   host.prefix[0] = 0;
   host.prefix[1] = (long long)g->tiles_x * g->tiles_y * g->Nz;
   const int slot = (&F == &g->Z) ? 1 : 0;
@@ -503,6 +504,9 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   key.shape = g->shape;
   key.ctas = G;
   key.desc = dslot;
+  key.skip = g->debug_skip_plane;
+  key.spin = g->spin_limit;
+  for (int j = 0; j <= kMaxR; ++j) key.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
   const bool reuse = use_graph && g->graph_valid && memcmp(&key, &g->gkey, sizeof(key)) == 0;
   if (g->profiling) cudaEventRecord(g->ev0, g->stream);
   const int cur0 = F.cur;
@@ -520,17 +524,14 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       StepOverride ov;
       memset(&ov, 0, sizeof(ov));
       ov.cur = (cur0 + t) & 1;
+      ov.spin_limit = g->spin_limit;
+      ov.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
+      for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
       ov.inj_row = rs.inj_row0 + rs.inj_row_step * t;
       ov.rec_row = rs.rec_row0 + rs.rec_row_step * t;
       if (mode == kModeStoreE) ov.e_out = rs.e_base + size_t(t) * g->ncell;
       if (mode == kModeAdjoint)
         ov.e_in = rs.e_base + size_t(rs.e_idx0 + rs.e_idx_step * t) * g->ncell;
-      if (t == 1 && g->debug_skip_plane >= 0) {
-        // the test hook applies to the first step only
-        host.d.args.debug_skip_plane = -1;
-        e = cudaMemcpyAsync(dslot, &host, sizeof(host), cudaMemcpyHostToDevice, g->stream);
-        if (e) return cuda_fail(e, "descriptor upload");
-      }
       e = launch_sweep(g->R, g->shape, mode, dshot, dprefix, 1, ov, G, g->stream);
       if (e) {
         if (use_graph) {

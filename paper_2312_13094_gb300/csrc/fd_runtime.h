@@ -61,6 +61,9 @@ struct GraphKey {
   TileShape shape;
   int ctas;
   void* desc;
+  int skip;
+  long long spin;
+  float c[kMaxR + 1];
 };
 
 constexpr int kNumShapes = 4;
