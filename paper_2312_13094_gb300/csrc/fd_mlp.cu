@@ -400,7 +400,7 @@ fd_status fd_mlp_create(int32_t device, const float* params, fd_mlp* out) {
   fd_mlp net = new fd_mlp_s();
   net->device = device;
   fd_status st = FD_OK;
-  e = cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking);
+  e = cudaStreamCreateWithFlags(&net->stream, cudaStreamDefault);  // see fd_create_grid
   float** bufs[4] = {&net->p, &net->g, &net->m, &net->v};
   for (int i = 0; i < 4 && !e; ++i) e = dev_alloc(reinterpret_cast<void**>(bufs[i]), NPARAM * 4);
   if (!e) e = dev_alloc(reinterpret_cast<void**>(&net->loss), 16);

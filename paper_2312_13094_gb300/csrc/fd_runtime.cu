@@ -681,7 +681,8 @@ fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
   if (d->stream) {
     g->stream = static_cast<cudaStream_t>(d->stream);
   } else {
-    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    // blocking: ordered after work the caller queued on the legacy default stream
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamDefault);
     if (e) st = cuda_fail(e, "stream create");
     g->own_stream = true;
   }

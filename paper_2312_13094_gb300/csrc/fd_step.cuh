@@ -143,12 +143,6 @@ __device__ __forceinline__ float lane(const float4& v, int i) {
 
 // One CTA: the xy tile (tile_x, tile_y), output planes [zbeg, zend).  All
 // threads of the CTA must call this with the same arguments.
-//
-// Pipeline: thread 0 issues the TMA loads.  Each ring slot has a "full"
-// mbarrier (completed by the TMA bytes) and an "empty" mbarrier on which
-// every warp arrives once it no longer reads the slot; thread 0 waits for a
-// slot's empty phase before reloading it, so no CTA-wide barrier is needed
-// per plane and warps only wait for the data they use.
 template <int R, int TX, int TY, int PF, int MODE>
 __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            const CUtensorMap* tm_prev,
@@ -160,8 +154,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            unsigned char* smem) {
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
-  constexpr int NWARP = C::NT / 32;
-  constexpr unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x;
   const int tx = tid % TX;
   const int ty = tid / TX;
@@ -170,77 +162,48 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   if (zbeg >= zend) return;
   const int zl = zend - zbeg;
   const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
+  const long long limit = ov.spin_limit;
   // once any CTA has recorded a failed wait, later columns and launches of
   // the same run return at once instead of waiting again (read by one
   // thread and shared, so the whole CTA takes the same branch)
   __shared__ int s_abort;
-  __shared__ volatile int s_bad;
-  if (tid == 0) {
-    s_abort = *reinterpret_cast<volatile const int*>(a.err);
-    s_bad = 0;
-  }
+  if (tid == 0) s_abort = *reinterpret_cast<volatile const int*>(a.err);
   __syncthreads();
   if (s_abort) return;
 
-  // scalars used on every plane: grid sizes in registers (the barrier waits
-  // clobber memory, which would otherwise reload them from shared memory);
-  // weights, wait limit and test hook straight from the launch parameter
-  const long long limit = ov.spin_limit;
-  const int Nx = a.Nx, Ny = a.Ny, pitch = a.pitch, nbl = a.nbl, nzp = a.nz;
-  const float bscale = a.bscale;
-  const float* cc = ov.c;
-  const int skip = ov.debug_skip_plane;
-
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t full_u = sbase + C::OFF_BAR;
-  const uint32_t full_a = full_u + 8 * C::SU;
-  const uint32_t empty_u = full_a + 8 * C::SA;
-  const uint32_t empty_a = empty_u + 8 * C::SU;
+  const uint32_t bar_u0 = sbase + C::OFF_BAR;
+  const uint32_t bar_a0 = bar_u0 + 8 * C::SU;
   const float* ubuf = reinterpret_cast<const float*>(smem);
   const float* pbuf = reinterpret_cast<const float*>(smem + C::OFF_P);
   const float* abuf = reinterpret_cast<const float*>(smem + C::OFF_A);
   const float* cbuf = reinterpret_cast<const float*>(smem + C::OFF_C);
 
   if (tid == 0) {
-    for (int s = 0; s < C::SU; ++s) {
-      mbar_init(full_u + 8 * s, 1);
-      mbar_init(empty_u + 8 * s, NWARP);
-    }
-    for (int s = 0; s < C::SA; ++s) {
-      mbar_init(full_a + 8 * s, 1);
-      mbar_init(empty_a + 8 * s, NWARP);
-    }
+    for (int s = 0; s < C::SU; ++s) mbar_init(bar_u0 + 8 * s, 1);
+    for (int s = 0; s < C::SA; ++s) mbar_init(bar_a0 + 8 * s, 1);
     fence_mbar_init();
   }
   __syncthreads();
 
   // producer state (meaningful in thread 0 only)
   int ju_next = 0, ia_next = 0;
-  bool bad = false;
   auto issue_u = [&](int j) {
     if (j >= J) return;
-    const int slot = j % C::SU;
-    if (j >= C::SU) {  // the slot's previous plane must have been released
-      bad |= !mbar_wait(empty_u + 8 * slot, ((j / C::SU) - 1) & 1, limit);
-      if (bad) return;
-    }
     ju_next = j + 1;
     const int z = zbeg - R + j;
-    if (skip >= 0 && z == skip) return;
-    const uint32_t bar = full_u + 8 * slot;
+    if (ov.debug_skip_plane >= 0 && z == ov.debug_skip_plane) return;
+    const int slot = j % C::SU;
+    const uint32_t bar = bar_u0 + 8 * slot;
     mbar_expect_tx(bar, C::UBYTES);
     tma_load_3d(sbase + slot * C::UPITCH, tm_halo, x0 - C::RX, y0 - R, z, bar);
   };
   auto issue_a = [&](int i) {
     if (i >= zl) return;
-    const int slot = i % C::SA;
-    if (i >= C::SA) {
-      bad |= !mbar_wait(empty_a + 8 * slot, ((i / C::SA) - 1) & 1, limit);
-      if (bad) return;
-    }
     ia_next = i + 1;
     const int z = zbeg + i;
-    const uint32_t bar = full_a + 8 * slot;
+    const int slot = i % C::SA;
+    const uint32_t bar = bar_a0 + 8 * slot;
     mbar_expect_tx(bar, (2 + NC) * C::TBYTES);
     tma_load_3d(sbase + C::OFF_P + slot * C::TPITCH, tm_prev, x0, y0, z, bar);
     tma_load_3d(sbase + C::OFF_A + slot * C::TPITCH, tm_A, x0, y0, z, bar);
@@ -248,11 +211,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     for (int j = 0; j < NC; ++j)  // coefficient field j sits j*Nz planes further
       tma_load_3d(sbase + C::OFF_C + (slot * NC + j) * C::TPITCH, tm_C, x0, y0,
                   z + j * a.Nz, bar);
-  };
-  // a warp releases a slot once all its lanes are done with it
-  auto release = [&](uint32_t bar) {
-    __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(bar);
   };
 
   if (tid == 0) {
@@ -262,27 +220,21 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
 
   const int crow = (ty + R) * C::W + 4 * tx + C::RX;  // centre float offset
   float4 q[2 * R + 1];
+  bool bad = false;
 
-  // warm-up: planes zbeg-R .. zbeg+R-1 into the queue; the first R are not
-  // needed again and are released at once
 #pragma unroll
   for (int j = 0; j < 2 * R; ++j) {
     const int slot = j % C::SU;
-    bad |= !mbar_wait(full_u + 8 * slot, (j / C::SU) & 1, limit);
-    bad = __any_sync(FULL, bad);
-    if (bad) {
-      s_bad = 1;
-      goto fail;
-    }
+    bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, limit);
     q[j] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
     if (j < R) {
-      release(empty_u + 8 * slot);
+      if (__syncthreads_or(bad)) goto fail;
       if (tid == 0) issue_u(j + C::SU);
     }
   }
 
   {
-    // entry ranges of this tile, skipping entries below this z range
+    // entry ranges of this tile, skipping entries below this z chunk
     const int tile = tile_y * a.tiles_x + tile_x;
     int ip = 0, iend = 0, rp = 0, rend = 0;
     if (a.inj_start) {
@@ -298,33 +250,30 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
 
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx;
-    const bool row_ok = gy < Ny;
-    const bool col_ok = gx < Nx;
-    const int nxp = a.nx, nyp = a.ny;
-    const float c0x3 = 3.0f * cc[0];
-    // ring positions of plane jk (xy halo) and of aux tile ik, advanced
-    // incrementally; the queue head jn = jk + R sits R slots further
-    int s_k = R % C::SU, p_k = (R / C::SU) & 1;
-    int s_i = 0, p_i = 0;
+    const bool row_ok = gy < a.Ny;
+    const bool col_ok = gx < a.Nx;
+    const int dyv = sponge_depth(gy, a.nbl, a.ny);
+    float dxx[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int d = sponge_depth(gx + l, a.nbl, a.nx);
+      dxx[l] = static_cast<float>(d * d + dyv * dyv);
+    }
+    const float c0x3 = 3.0f * ov.c[0];
 
     for (int k = zbeg; k < zend; ++k) {
       const int jk = k - zbeg + R;
       const int ik = k - zbeg;
-      int s_n = s_k + R, p_n = p_k;
-      if (s_n >= C::SU) {
-        s_n -= C::SU;
-        p_n ^= 1;
+      const int jn = jk + R;
+      {
+        const int slot = jn % C::SU;
+        bad |= !mbar_wait(bar_u0 + 8 * slot, (jn / C::SU) & 1, limit);
+        q[2 * R] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
       }
-      bad |= !mbar_wait(full_u + 8 * s_n, p_n, limit);
-      bad |= !mbar_wait(full_a + 8 * s_i, p_i, limit);
-      bad = __any_sync(FULL, bad || s_bad);  // warp-uniform decision
-      if (bad) {
-        s_bad = 1;
-        goto fail;
-      }
-      q[2 * R] = *reinterpret_cast<const float4*>(ubuf + s_n * (C::UPITCH / 4) + crow);
+      const int aslot = ik % C::SA;
+      bad |= !mbar_wait(bar_a0 + 8 * aslot, (ik / C::SA) & 1, limit);
 
-      const float* P = ubuf + s_k * (C::UPITCH / 4);
+      const float* P = ubuf + (jk % C::SU) * (C::UPITCH / 4);
       float xr[4 * C::NROW4];
 #pragma unroll
       for (int m = 0; m < C::NROW4; ++m) {
@@ -334,6 +283,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         xr[4 * m + 2] = v.z;
         xr[4 * m + 3] = v.w;
       }
+      const int aslot_c = ik % C::SA;
       float lap[4];
       if (MODE == kModePerCell) {
         // per-cell weights c_1..c_R from the staged coefficient tiles,
@@ -342,7 +292,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
 #pragma unroll
         for (int jj = 1; jj <= R; ++jj) {
           const float4 cv = *reinterpret_cast<const float4*>(
-              cbuf + (s_i * NC + (jj - 1)) * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+              cbuf + (aslot_c * NC + (jj - 1)) * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
           const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
           const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
 #pragma unroll
@@ -364,12 +314,13 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         for (int jj = 1; jj <= R; ++jj) {
           const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
           const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
+          const float cj = ov.c[jj];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
             const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
             const float sy = lane(ym, l) + lane(yp, l);
             const float sz = lane(q[R - jj], l) + lane(q[R + jj], l);
-            lap[l] = fmaf(cc[jj], (sx + sy) + sz, lap[l]);
+            lap[l] = fmaf(cj, (sx + sy) + sz, lap[l]);
           }
         }
       }
@@ -387,17 +338,14 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         ++ip;
       }
 
-      const int aoff = s_i * (C::TPITCH / 4) + ty * C::BX + 4 * tx;
-      const float4 up = *reinterpret_cast<const float4*>(pbuf + aoff);
-      const float4 Av = *reinterpret_cast<const float4*>(abuf + aoff);
-      const int dz = sponge_depth(k, nbl, nzp);
-      const int dy = sponge_depth(gy, nbl, nyp);
-      const float dyz = static_cast<float>(dz * dz + dy * dy);
+      const float4 up = *reinterpret_cast<const float4*>(pbuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+      const float4 Av = *reinterpret_cast<const float4*>(abuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
+      const int dz = sponge_depth(k, a.nbl, a.nz);
+      const float dzz = static_cast<float>(dz * dz);
       float res[4], ev[4];
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        const int dx = sponge_depth(gx + l, nbl, nxp);
-        const float b = bscale * (static_cast<float>(dx * dx) + dyz);
+        const float b = a.bscale * (dxx[l] + dzz);
         const float uc = lane(q[R], l);
         // the same explicit roundings in every mode, so that a recomputed
         // segment reproduces the stored states bit for bit
@@ -407,22 +355,21 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         // inside the layer divide by 1+b (fast reciprocal; select, no branch)
         const float td = __fdividef(t, 1.0f + b);
         t = (b != 0.0f) ? td : t;
-        res[l] = (gx + l < Nx) ? t : 0.0f;
-        ev[l] = (gx + l < Nx) ? e : 0.0f;
+        res[l] = (gx + l < a.Nx) ? t : 0.0f;
+        ev[l] = (gx + l < a.Nx) ? e : 0.0f;
       }
       if (row_ok && col_ok) {
-        const size_t off = (static_cast<size_t>(k) * Ny + gy) * pitch + gx;
+        const size_t off = (static_cast<size_t>(k) * a.Ny + gy) * a.pitch + gx;
         *reinterpret_cast<float4*>(out + off) = make_float4(res[0], res[1], res[2], res[3]);
         if (MODE == kModeStoreE)
           *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
         if (MODE == kModeAdjoint) {
-          const float idt2 = a.inv_dt2;
           const float4 ein = *reinterpret_cast<const float4*>(a.e_in + off);
           float4 g = *reinterpret_cast<float4*>(a.grad + off);
-          g.x -= q[R].x * ein.x * idt2;
-          g.y -= q[R].y * ein.y * idt2;
-          g.z -= q[R].z * ein.z * idt2;
-          g.w -= q[R].w * ein.w * idt2;
+          g.x -= q[R].x * ein.x * a.inv_dt2;
+          g.y -= q[R].y * ein.y * a.inv_dt2;
+          g.z -= q[R].z * ein.z * a.inv_dt2;
+          g.w -= q[R].w * ein.w * a.inv_dt2;
           *reinterpret_cast<float4*>(a.grad + off) = g;
         }
       }
@@ -432,65 +379,49 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       {
         int rq = rp;
         while (rq < rend && a.recs[rq].z == k) ++rq;
-        if (rq > rp) {
-          const int s1 = (s_k + 1 == C::SU) ? 0 : s_k + 1;
-          const float* P1 = ubuf + s1 * (C::UPITCH / 4);
-          for (int e = rp + tid; e < rq; e += C::NT) {
-            const RecEntry r = a.recs[e];
-            const int o = (r.ly + R) * C::W + r.lx + C::RX;
-            const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
-            const float p0 = gy0 * (gx0 * P[o] + r.fx * P[o + 1]) +
-                             r.fy * (gx0 * P[o + C::W] + r.fx * P[o + C::W + 1]);
-            const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
-                             r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
-            a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
-                (1.0f - r.fz) * p0 + r.fz * p1;
-          }
+        const float* P1 = ubuf + ((jk + 1) % C::SU) * (C::UPITCH / 4);
+        for (int e = rp + tid; e < rq; e += C::NT) {
+          const RecEntry r = a.recs[e];
+          const int o = (r.ly + R) * C::W + r.lx + C::RX;
+          const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
+          const float p0 = gy0 * (gx0 * P[o] + r.fx * P[o + 1]) +
+                           r.fy * (gx0 * P[o + C::W] + r.fx * P[o + C::W + 1]);
+          const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
+                           r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
+          a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
+              (1.0f - r.fz) * p0 + r.fz * p1;
         }
         rp = rq;
       }
 
-      // this warp is done with plane jk and aux tile ik
-      release(empty_u + 8 * s_k);
-      release(empty_a + 8 * s_i);
+      if (__syncthreads_or(bad)) goto fail;
       if (tid == 0) {
         issue_u(jk + C::SU);
         issue_a(ik + C::SA);
-        if (bad) s_bad = 1;
       }
-      if (++s_k == C::SU) { s_k = 0; p_k ^= 1; }
-      if (++s_i == C::SA) { s_i = 0; p_i ^= 1; }
 #pragma unroll
       for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
     }
   }
-  goto done;
+  // every issued copy has been waited for; release the barriers so the
+  // shared memory can host the next column
+  if (tid == 0) {
+    for (int s = 0; s < C::SU; ++s) mbar_inval(bar_u0 + 8 * s);
+    for (int s = 0; s < C::SA; ++s) mbar_inval(bar_a0 + 8 * s);
+  }
+  __syncthreads();
+  return;
 
 fail:
   if (tid == 0) {
     atomicOr(a.err, 1);
     // wait (bounded) for every copy this CTA still has in flight
     for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
-      if (skip >= 0 && zbeg - R + j == skip) continue;
-      mbar_wait(full_u + 8 * (j % C::SU), (j / C::SU) & 1, limit);
+      if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
+      mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, limit);
     }
     for (int i = max(0, ia_next - C::SA); i < ia_next; ++i)
-      mbar_wait(full_a + 8 * (i % C::SA), (i / C::SA) & 1, limit);
-  }
-
-done:
-  // every issued copy has been waited for; release the barriers so the
-  // shared memory can host the next column
-  __syncthreads();
-  if (tid == 0) {
-    for (int s = 0; s < C::SU; ++s) {
-      mbar_inval(full_u + 8 * s);
-      mbar_inval(empty_u + 8 * s);
-    }
-    for (int s = 0; s < C::SA; ++s) {
-      mbar_inval(full_a + 8 * s);
-      mbar_inval(empty_a + 8 * s);
-    }
+      mbar_wait(bar_a0 + 8 * (i % C::SA), (i / C::SA) & 1, limit);
   }
 }
 

@@ -83,12 +83,30 @@ def training_samples(fine, coarse, ncell: int = 16384, ntimes: int = 8, seed: in
     ntc = coarse["nt"]
     times = np.sort(rng.choice(np.arange(ntc // 2, ntc - 1), ntimes, replace=False))
     src_c = np.round(np.asarray(coarse["src"][0]) / coarse["h"]).astype(int)
+    vf = fine["v"]
+    nf = vf.shape
     cells_c = []
-    while len(cells_c) < ncell:
+    tries = 0
+    while len(cells_c) < ncell and tries < 200:
+        tries += 1
         c = rng.integers(0, nc[0], size=(ncell, 3))
         d = np.abs(c - src_c[None, :]).max(axis=1)
-        cells_c.extend(c[d >= min_src_dist].tolist())
-    cells_c = np.array(cells_c[:ncell], dtype=np.int32)        # (x, y, z) coarse
+        c = c[d >= min_src_dist]
+        # keep cells whose coarse stencil (radius 4) sees a homogeneous medium:
+        # only there can a set of weights per cell reproduce the fine solution
+        vc = vf[2 * c[:, 2], 2 * c[:, 1], 2 * c[:, 0]]
+        ok = np.ones(len(c), bool)
+        for a in range(3):
+            for j in (-8, -4, 4, 8):
+                p = 2 * c.copy()
+                p[:, a] = np.clip(p[:, a] + j, 0, nf[2 - a] - 1)
+                vn = vf[p[:, 2], p[:, 1], p[:, 0]]
+                ok &= np.abs(vn - vc) <= 0.01 * vc
+        cells_c.extend(c[ok].tolist())
+    cells_c = np.array(cells_c[:ncell], dtype=np.int32).reshape(-1, 3)  # (x, y, z) coarse
+    ncell = len(cells_c)
+    if ncell == 0:
+        raise ValueError("no homogeneous cells to sample")
     cells_f = np.ascontiguousarray(2 * cells_c + nbl_f, dtype=np.int32)  # padded fine
     vel = torch.from_numpy(np.ascontiguousarray(
         fine["v"][2 * cells_c[:, 2], 2 * cells_c[:, 1], 2 * cells_c[:, 0]],
@@ -114,7 +132,7 @@ def training_samples(fine, coarse, ncell: int = 16384, ntimes: int = 8, seed: in
             fd.check(fd.fd_mlp_make_samples(ncell, snaps[0].data_ptr(), snaps[1].data_ptr(),
                                             snaps[2].data_ptr(), vel.data_ptr(),
                                             coarse["h"], coarse["dt"], coarse["f0"],
-                                            1e-3 * ms + 1e-30, s.data_ptr()),
+                                            ms + 1e-30, s.data_ptr()),
                      "fd_mlp_make_samples")
             out.append(s)
     return torch.cat(out)
