@@ -81,7 +81,11 @@ def training_samples(fine, coarse, ncell: int = 16384, ntimes: int = 8, seed: in
     nbl_f = fine["nbl"]
     rng = np.random.default_rng(seed)
     ntc = coarse["nt"]
-    times = np.sort(rng.choice(np.arange(ntc // 2, ntc - 1), ntimes, replace=False))
+    # coarse times at least two coarse steps apart, so that the fine-step
+    # triples (2t-2, 2t, 2t+2) of different times never overlap
+    cand = np.arange(ntc // 2, ntc - 1, 2)
+    times = np.sort(rng.choice(cand, min(ntimes, len(cand)), replace=False))
+    times = times[np.concatenate([[True], np.diff(times) >= 2])]
     src_c = np.round(np.asarray(coarse["src"][0]) / coarse["h"]).astype(int)
     vf = fine["v"]
     nf = vf.shape
