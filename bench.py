@@ -210,6 +210,9 @@ def run_ours(args, w, world, rank, local):
     nrec = len(w["rec"])
     with torch.cuda.stream(stream):
         g = fd.Grid.from_workload(w, device=local, stream=stream.cuda_stream)
+        if args.tile:
+            tx, ty, ctas = (int(v) for v in args.tile.split(","))
+            g.set_tile(tx, ty, ctas)
         v_dev = torch.from_numpy(w["v"]).cuda()
         wav_dev = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
         rec_dev = torch.zeros((nt, nrec), device="cuda")
@@ -476,6 +479,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--tile", default="", help="tile_x,tile_y,ctas for fd_set_tile")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.workload != "headline":

@@ -194,14 +194,36 @@ int sweep_ctas(int R, const TileShape& t, int mode) {
 const TileShape kShapes[kNumShapes] = {
     {16, 16, 2, 0}, {32, 8, 2, 0}, {8, 32, 2, 0}, {16, 8, 3, 0}};
 
-// Default tile: 64x16 for the narrow stencils, 128x8 when the halo is wide.
+// Default tile.  A shape whose columns can all be resident at once (and fill
+// at least half of the slots) runs as lockstep columns that share halos in
+// L2; among those the one with the most resident warps wins, smaller CTAs on
+// a tie (their per-plane barrier is cheaper).  Without such a shape, the one
+// with the most resident warps runs the equal-share sweep.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
-  (void)Nx;
-  (void)Ny;
   (void)Nz;
-  TileShape t = kShapes[0];
-  if (R >= 6) t = kShapes[1];
-  return t;
+  int best = -1, best_sweep = 0;
+  long long best_w = -1, best_sweep_w = -1;
+  for (int i = 0; i < kNumShapes; ++i) {
+    const TileShape& t = kShapes[i];
+    const int nt = t.tx * t.ty;
+    const long long T = (long long)((Nx + 4 * t.tx - 1) / (4 * t.tx)) *
+                        ((Ny + t.ty - 1) / t.ty);
+    const long long slots = sweep_ctas(R, t, kModeForward);
+    const long long sweep_w = slots * nt / 32;
+    if (sweep_w > best_sweep_w ||
+        (sweep_w == best_sweep_w && nt < kShapes[best_sweep].tx * kShapes[best_sweep].ty)) {
+      best_sweep_w = sweep_w;
+      best_sweep = i;
+    }
+    if (T <= slots && 2 * T >= slots) {
+      const long long w = T * nt / 32;
+      if (w > best_w || (w == best_w && nt < kShapes[best].tx * kShapes[best].ty)) {
+        best_w = w;
+        best = i;
+      }
+    }
+  }
+  return kShapes[best >= 0 ? best : best_sweep];
 }
 
 void set_shape(fd_grid g, TileShape t) {

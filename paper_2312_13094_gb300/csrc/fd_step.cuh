@@ -130,6 +130,28 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 3D tile load whose lines are marked first for eviction from L2: for
+// tiles that are read exactly once (u^{n-1}, A), so that they do not push out
+// the u^n planes that neighbouring columns are about to read as halos.
+__device__ __forceinline__ void tma_load_3d_stream(uint32_t dst, const CUtensorMap* map,
+                                                   int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::"
+      "bytes.L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], pol;\n\t}" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Streaming 128-bit store (evict-first): u^{n+1} is not read again in this
+// launch.
+__device__ __forceinline__ void st_stream(float* p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
 __device__ __forceinline__ int sponge_depth(int g, int nbl, int n) {
   int d = nbl - g;
   int e = g - (n + nbl - 1);
@@ -205,8 +227,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     const int slot = i % C::SA;
     const uint32_t bar = bar_a0 + 8 * slot;
     mbar_expect_tx(bar, (2 + NC) * C::TBYTES);
-    tma_load_3d(sbase + C::OFF_P + slot * C::TPITCH, tm_prev, x0, y0, z, bar);
-    tma_load_3d(sbase + C::OFF_A + slot * C::TPITCH, tm_A, x0, y0, z, bar);
+    tma_load_3d_stream(sbase + C::OFF_P + slot * C::TPITCH, tm_prev, x0, y0, z, bar);
+    tma_load_3d_stream(sbase + C::OFF_A + slot * C::TPITCH, tm_A, x0, y0, z, bar);
 #pragma unroll
     for (int j = 0; j < NC; ++j)  // coefficient field j sits j*Nz planes further
       tma_load_3d(sbase + C::OFF_C + (slot * NC + j) * C::TPITCH, tm_C, x0, y0,
@@ -360,7 +382,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       }
       if (row_ok && col_ok) {
         const size_t off = (static_cast<size_t>(k) * a.Ny + gy) * a.pitch + gx;
-        *reinterpret_cast<float4*>(out + off) = make_float4(res[0], res[1], res[2], res[3]);
+        st_stream(out + off, res[0], res[1], res[2], res[3]);
         if (MODE == kModeStoreE)
           *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
         if (MODE == kModeAdjoint) {
