@@ -453,6 +453,8 @@ def run_learned(args):
     print(json.dumps({
         "metric": "receiver rel. L2 vs fine SO16 (learned coarse)", "value": learned,
         "unit": "rel. L2", "higher_is_better": False, "plain_coarse": plain,
+        "plain_coarse_so16": float(np.mean([r["plain16"] for r in rows])),
+        "ms_coarse_plain_so16": float(np.mean([r["ms_plain16"] for r in rows])),
         "ms_fine": float(np.mean([r["ms_fine"] for r in rows])),
         "ms_coarse_plain": float(np.mean([r["ms_plain"] for r in rows])),
         "ms_coarse_learned": float(np.mean([r["ms_learned"] for r in rows])),
@@ -480,6 +482,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--tile", default="", help="tile_x,tile_y,ctas for fd_set_tile")
+    ap.add_argument("--space-order", type=int, default=8)
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.workload != "headline":
@@ -490,6 +493,9 @@ def main():
         return
     from paper_2312_13094_gb300 import workloads as wl
     w = wl.acoustic_512(n=args.n, nt=args.nt)
+    if args.space_order != 8:
+        w["space_order"] = args.space_order
+        w["name"] = w["name"].replace("SO8", f"SO{args.space_order}")
     if args.impl == "reference":
         run_reference(args, w, world, rank)
     else:

@@ -166,7 +166,8 @@ fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
 /* Chooses the stencil tile (tile_x x tile_y points per CTA column) and the
  * number of persistent CTAs of each step launch (0: as many as are resident
  * on all SMs at once).  Each CTA sweeps an equal contiguous share of the
- * grid's (tile, z plane) units.  Compiled tiles: 64x16, 128x8, 32x32, 64x8.
+ * grid's (tile, z plane) units.  Compiled tiles: 64x16, 128x8, 32x16, 64x8,
+ * 32x8.
  * Errors: FD_ERR_ARG for a tile that is not compiled or ctas < 0. */
 fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas);
 

@@ -192,7 +192,7 @@ int sweep_ctas(int R, const TileShape& t, int mode) {
 }
 
 const TileShape kShapes[kNumShapes] = {
-    {16, 16, 2, 0}, {32, 8, 2, 0}, {8, 32, 2, 0}, {16, 8, 3, 0}};
+    {16, 16, 2, 0}, {32, 8, 2, 0}, {8, 16, 1, 0}, {16, 8, 2, 0}, {8, 8, 1, 0}};
 
 // Default tile.  A shape whose columns can all be resident at once (and fill
 // at least half of the slots) runs as lockstep columns that share halos in

@@ -66,7 +66,7 @@ struct GraphKey {
   float c[kMaxR + 1];
 };
 
-constexpr int kNumShapes = 4;
+constexpr int kNumShapes = 5;
 extern const TileShape kShapes[kNumShapes];
 
 }  // namespace fd

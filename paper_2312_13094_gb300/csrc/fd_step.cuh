@@ -53,12 +53,17 @@ struct Cfg {
   static_assert(W <= 256 && H <= 256, "TMA box too large");
 };
 
+// Threads per SM that the launch bounds aim for: the register queue of the
+// wide stencils (2R+1 float4 per thread) needs more registers per thread.
+constexpr int threads_per_sm(int R) { return R <= 4 ? 768 : 512; }
+
 // Prefetch depth of a tile shape: the deepest ring (1..6 planes beyond the
 // R+1 in use) whose shared memory still lets the CTAs that the launch bounds
-// admit be resident together (three CTAs of 256 threads or six of 128).
+// admit be resident together (768 threads per SM for R <= 4: three CTAs of
+// 256 threads, six of 128 or twelve of 64; 512 for the wider stencils).
 template <int R, int TX, int TY, int NC>
 constexpr int auto_pf() {
-  const uint32_t budget = (TX * TY >= 256) ? 72u * 1024u : 36u * 1024u;
+  const uint32_t budget = 219u * 1024u / (threads_per_sm(R) / (TX * TY));
   const int rx = ((R + 3) / 4) * 4;
   const uint32_t up = ((4 * TX + 2 * rx) * (TY + 2 * R) * 4 + 127) / 128 * 128;
   const uint32_t tp = (4 * TX * TY * 4 + 127) / 128 * 128;
@@ -454,7 +459,7 @@ fail:
 // the number of resident CTAs every SM streams the same number of planes and
 // no CTA waits for a second wave.
 template <int R, int TX, int TY, int PF, int MODE>
-__global__ void __launch_bounds__(TX* TY, (TX * TY >= 256) ? 3 : 6)
+__global__ void __launch_bounds__(TX* TY, threads_per_sm(R) / (TX * TY))
     sweep_kernel(const ShotDesc* __restrict__ shots, const long long* __restrict__ prefix,
                  int nshots, const __grid_constant__ StepOverride ov) {
   extern __shared__ unsigned char smem_raw[];

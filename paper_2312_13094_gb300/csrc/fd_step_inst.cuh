@@ -57,7 +57,7 @@ int occupancy_one() {
 
 // Tile shapes compiled for every radius: (threads in x, rows); the prefetch
 // depth of each follows from its shared-memory budget (auto_pf).
-#define FD_FOR_EACH_SHAPE(X) X(16, 16) X(32, 8) X(8, 32) X(16, 8)
+#define FD_FOR_EACH_SHAPE(X) X(16, 16) X(32, 8) X(8, 16) X(16, 8) X(8, 8)
 
 #if FD_R == 4
 #define FD_PERCELL(F, TX, TY) \

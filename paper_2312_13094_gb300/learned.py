@@ -221,7 +221,9 @@ def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True):
         rf, tf = run_forward(fine, device, timed=timed)
         ref = rf[::2]
         rp, tp = run_forward(coarse, device, timed=timed)
+        r16, t16 = run_forward(coarse, device, space_order=16, timed=timed)
         rl, tlr = run_forward(coarse, device, net=net.handle, timed=timed)
-        rows.append(dict(seed=s, plain=rel_l2(rp, ref), learned=rel_l2(rl, ref),
-                         ms_fine=tf, ms_plain=tp, ms_learned=tlr))
+        rows.append(dict(seed=s, plain=rel_l2(rp, ref), plain16=rel_l2(r16, ref),
+                         learned=rel_l2(rl, ref), ms_fine=tf, ms_plain=tp, ms_plain16=t16,
+                         ms_learned=tlr))
     return rows

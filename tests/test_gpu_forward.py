@@ -101,7 +101,7 @@ def test_tile_shapes_and_cta_counts_agree_bitwise(fd, so):
     ref_rec, ref_u = run_gpu(fd, w, tile=(64, 16), ctas=0)
     orec, ou = run_oracle(w)
     assert rel(ref_rec, orec) <= TOL and rel(ref_u, ou) <= TOL
-    for tile in [(64, 16), (128, 8), (32, 32), (64, 8)]:
+    for tile in [(64, 16), (128, 8), (32, 16), (64, 8), (32, 8)]:
         for ctas in (0, 1, 7, 100, 999):
             rec, u = run_gpu(fd, w, tile=tile, ctas=ctas)
             np.testing.assert_array_equal(rec, ref_rec)
