@@ -51,16 +51,16 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload):
+def _traffic(workload, tile):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+    if it was taken on the current kernel source with the same tile; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload)
-    if not e or e.get("kernel_hash") != _kernel_hash():
+    if not e or e.get("kernel_hash") != _kernel_hash() or list(e.get("tile", [])) != list(tile):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -292,8 +292,8 @@ def run_ours(args, w, world, rank, local):
         "data": "synthetic", "config": _config(w),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": _traffic(w["name"]),
-                     "kernel": "fd::step_kernel (avg over the timed launches)",
+                     "traffic": _traffic(w["name"], [info["tile_x"], info["tile_y"]]),
+                     "kernel": "fd::sweep_kernel (avg over the timed launches)",
                      "algorithmic_bytes_per_launch": ALGO_BYTES_PER_POINT * npts,
                      "avg_launch_ms": avg_launch_ms},
         "clocks": clk,

@@ -196,30 +196,36 @@ const TileShape kShapes[kNumShapes] = {
 
 // Default tile.  A shape whose columns can all be resident at once (and fill
 // at least half of the slots) runs as lockstep columns that share halos in
-// L2; among those the one with the most resident warps wins, smaller CTAs on
-// a tie (their per-plane barrier is cheaper).  Without such a shape, the one
-// with the most resident warps runs the equal-share sweep.
+// L2.  Lockstep columns land on the SMs as evenly as the block scheduler can
+// place them, so the slowest SM holds ceil(T / SMs) columns: among the
+// lockstep shapes the one with the fewest tile points on that SM wins, then
+// the wider tile, then the taller one.  Without a lockstep shape the widest
+// (then tallest) tile runs the equal-share sweep, whose shares are balanced by
+// construction.  Measured on GB300 (SO 8, Gpts/s): 592^3 lockstep 64x8 283,
+// 32x16 275, 128x8 256, 32x8 250, 64x16 245; 768^3 sweep 128x8 255, 64x16
+// 228, 64x8 203, 32x16 183, 32x8 148.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
   (void)Nz;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sms = std::max(1, sms);
+  auto wider = [](const TileShape& p, const TileShape& q) {  // p before q
+    return p.tx != q.tx ? p.tx > q.tx : p.ty > q.ty;
+  };
   int best = -1, best_sweep = 0;
-  long long best_w = -1, best_sweep_w = -1;
+  long long best_load = 0;
   for (int i = 0; i < kNumShapes; ++i) {
     const TileShape& t = kShapes[i];
-    const int nt = t.tx * t.ty;
-    const long long T = (long long)((Nx + 4 * t.tx - 1) / (4 * t.tx)) *
-                        ((Ny + t.ty - 1) / t.ty);
+    const int bx = 4 * t.tx, by = t.ty;
+    const long long T = (long long)((Nx + bx - 1) / bx) * ((Ny + by - 1) / by);
     const long long slots = sweep_ctas(R, t, kModeForward);
-    const long long sweep_w = slots * nt / 32;
-    if (sweep_w > best_sweep_w ||
-        (sweep_w == best_sweep_w && nt < kShapes[best_sweep].tx * kShapes[best_sweep].ty)) {
-      best_sweep_w = sweep_w;
-      best_sweep = i;
-    }
+    if (wider(t, kShapes[best_sweep])) best_sweep = i;
     if (T <= slots && 2 * T >= slots) {
-      const long long w = T * nt / 32;
-      if (w > best_w || (w == best_w && nt < kShapes[best].tx * kShapes[best].ty)) {
-        best_w = w;
+      const long long load = (T + sms - 1) / sms * (long long)(bx * by);
+      if (best < 0 || load < best_load || (load == best_load && wider(t, kShapes[best]))) {
         best = i;
+        best_load = load;
       }
     }
   }

@@ -25,6 +25,8 @@
 //    error, waits (bounded) for its own copies still in flight, and returns.
 #pragma once
 
+#include <climits>
+
 #include "fd_internal.h"
 
 namespace fd {
@@ -56,6 +58,11 @@ struct Cfg {
 // Threads per SM that the launch bounds aim for: the register queue of the
 // wide stencils (2R+1 float4 per thread) needs more registers per thread.
 constexpr int threads_per_sm(int R) { return R <= 4 ? 768 : 512; }
+
+// Planes per unrolled block of the z loop (see run_column).  One: on GB300
+// the 9-plane rotating body of SO 8 overflowed the instruction cache (234 vs
+// 280 Gpts/s on 592^3) and two planes per block ran 1.5 % slower than one.
+constexpr int zloop_unroll(int) { return 1; }
 
 // Prefetch depth of a tile shape: the deepest ring (1..6 planes beyond the
 // R+1 in use) whose shared memory still lets the CTAs that the launch bounds
@@ -170,6 +177,19 @@ __device__ __forceinline__ float lane(const float4& v, int i) {
 
 // One CTA: the xy tile (tile_x, tile_y), output planes [zbeg, zend).  All
 // threads of the CTA must call this with the same arguments.
+//
+// Ring bookkeeping.  u planes are numbered j = 0 .. J-1 (z = zbeg - R + j) and
+// live in slot j mod SU; u^{n-1}/A tiles i = 0 .. zl-1 (z = zbeg + i) in slot
+// i mod SA.  Output plane k (i = k - zbeg) reads the staged plane jk = i + R
+// for its x and y neighbours and takes plane jn = i + 2R into the register
+// queue; once every thread has passed the plane, thread 0 refills slot
+// jk mod SU with plane jk + SU and slot i mod SA with tile i + SA.  The slots
+// are tracked as byte offsets that advance by one pitch per plane.
+//
+// The z loop runs in blocks of U planes (zloop_unroll).  With U = 2R+1 the
+// queue rotates by register naming: plane jk + o sits in q[(s + R + o) mod
+// (2R+1)] at unrolled position s.  Otherwise the queue holds 2R+U entries,
+// plane jk + o sits in q[s + R + o], and the queue shifts by U after a block.
 template <int R, int TX, int TY, int PF, int MODE>
 __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            const CUtensorMap* tm_prev,
@@ -181,6 +201,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            unsigned char* smem) {
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
+  constexpr int NQ = 2 * R + 1;
+  constexpr int U = zloop_unroll(R);
+  constexpr bool ROT = (U == NQ);
+  constexpr int QN = ROT ? NQ : NQ + U - 1;
+  constexpr uint32_t URING = C::SU * C::UPITCH;
+  constexpr uint32_t ARING = C::SA * C::TPITCH;
   const int tid = threadIdx.x;
   const int tx = tid % TX;
   const int ty = tid / TX;
@@ -189,7 +215,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   if (zbeg >= zend) return;
   const int zl = zend - zbeg;
   const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
-  const long long limit = ov.spin_limit;
   // once any CTA has recorded a failed wait, later columns and launches of
   // the same run return at once instead of waiting again (read by one
   // thread and shared, so the whole CTA takes the same branch)
@@ -201,10 +226,10 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar_u0 = sbase + C::OFF_BAR;
   const uint32_t bar_a0 = bar_u0 + 8 * C::SU;
-  const float* ubuf = reinterpret_cast<const float*>(smem);
-  const float* pbuf = reinterpret_cast<const float*>(smem + C::OFF_P);
-  const float* abuf = reinterpret_cast<const float*>(smem + C::OFF_A);
-  const float* cbuf = reinterpret_cast<const float*>(smem + C::OFF_C);
+  const unsigned char* ubuf = smem;
+  const unsigned char* pbuf = smem + C::OFF_P;
+  const unsigned char* abuf = smem + C::OFF_A;
+  const unsigned char* cbuf = smem + C::OFF_C;
 
   if (tid == 0) {
     for (int s = 0; s < C::SU; ++s) mbar_init(bar_u0 + 8 * s, 1);
@@ -213,50 +238,50 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   }
   __syncthreads();
 
-  // producer state (meaningful in thread 0 only)
+  // producer (thread 0): next plane / tile to issue
   int ju_next = 0, ia_next = 0;
-  auto issue_u = [&](int j) {
+  auto issue_u = [&](int j, uint32_t uoff) {
     if (j >= J) return;
     ju_next = j + 1;
     const int z = zbeg - R + j;
     if (ov.debug_skip_plane >= 0 && z == ov.debug_skip_plane) return;
-    const int slot = j % C::SU;
-    const uint32_t bar = bar_u0 + 8 * slot;
+    const uint32_t bar = bar_u0 + 8 * (uoff / C::UPITCH);
     mbar_expect_tx(bar, C::UBYTES);
-    tma_load_3d(sbase + slot * C::UPITCH, tm_halo, x0 - C::RX, y0 - R, z, bar);
+    tma_load_3d(sbase + uoff, tm_halo, x0 - C::RX, y0 - R, z, bar);
   };
-  auto issue_a = [&](int i) {
+  auto issue_a = [&](int i, uint32_t aoff) {
     if (i >= zl) return;
     ia_next = i + 1;
     const int z = zbeg + i;
-    const int slot = i % C::SA;
-    const uint32_t bar = bar_a0 + 8 * slot;
+    const uint32_t bar = bar_a0 + 8 * (aoff / C::TPITCH);
     mbar_expect_tx(bar, (2 + NC) * C::TBYTES);
-    tma_load_3d_stream(sbase + C::OFF_P + slot * C::TPITCH, tm_prev, x0, y0, z, bar);
-    tma_load_3d_stream(sbase + C::OFF_A + slot * C::TPITCH, tm_A, x0, y0, z, bar);
+    tma_load_3d_stream(sbase + C::OFF_P + aoff, tm_prev, x0, y0, z, bar);
+    tma_load_3d_stream(sbase + C::OFF_A + aoff, tm_A, x0, y0, z, bar);
 #pragma unroll
     for (int j = 0; j < NC; ++j)  // coefficient field j sits j*Nz planes further
-      tma_load_3d(sbase + C::OFF_C + (slot * NC + j) * C::TPITCH, tm_C, x0, y0,
+      tma_load_3d(sbase + C::OFF_C + ((aoff / C::TPITCH) * NC + j) * C::TPITCH, tm_C, x0, y0,
                   z + j * a.Nz, bar);
   };
 
   if (tid == 0) {
-    for (int j = 0; j < C::SU; ++j) issue_u(j);
-    for (int i = 0; i < C::SA; ++i) issue_a(i);
+    for (int j = 0; j < C::SU; ++j) issue_u(j, j * C::UPITCH);
+    for (int i = 0; i < C::SA; ++i) issue_a(i, i * C::TPITCH);
   }
 
-  const int crow = (ty + R) * C::W + 4 * tx + C::RX;  // centre float offset
-  float4 q[2 * R + 1];
+  // byte offsets of the thread's own float4 in a staged plane / tile
+  const uint32_t crow = 4u * ((ty + R) * C::W + 4 * tx + C::RX);
+  const uint32_t ctile = 4u * (ty * C::BX + 4 * tx);
+  float4 q[QN];
   bool bad = false;
 
 #pragma unroll
   for (int j = 0; j < 2 * R; ++j) {
     const int slot = j % C::SU;
-    bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, limit);
-    q[j] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
+    bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, ov.spin_limit);
+    q[j] = *reinterpret_cast<const float4*>(ubuf + slot * C::UPITCH + crow);
     if (j < R) {
       if (__syncthreads_or(bad)) goto fail;
-      if (tid == 0) issue_u(j + C::SU);
+      if (tid == 0) issue_u(j + C::SU, slot * C::UPITCH);
     }
   }
 
@@ -274,11 +299,14 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       rend = a.rec_start[tile + 1];
       while (rp < rend && a.recs[rp].z < zbeg) ++rp;
     }
+    // plane of the next entry of each list (INT_MAX: none), kept in a
+    // register so that planes without entries touch neither list
+    int iz = ip < iend ? a.inj[ip].z : INT_MAX;
+    int rz = rp < rend ? a.recs[rp].z : INT_MAX;
 
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx;
-    const bool row_ok = gy < a.Ny;
-    const bool col_ok = gx < a.Nx;
+    const bool in_grid = gy < a.Ny && gx < a.Nx;
     const int dyv = sponge_depth(gy, a.nbl, a.ny);
     float dxx[4];
 #pragma unroll
@@ -287,147 +315,201 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       dxx[l] = static_cast<float>(d * d + dyv * dyv);
     }
     const float c0x3 = 3.0f * ov.c[0];
-
-    for (int k = zbeg; k < zend; ++k) {
-      const int jk = k - zbeg + R;
-      const int ik = k - zbeg;
-      const int jn = jk + R;
-      {
-        const int slot = jn % C::SU;
-        bad |= !mbar_wait(bar_u0 + 8 * slot, (jn / C::SU) & 1, limit);
-        q[2 * R] = *reinterpret_cast<const float4*>(ubuf + slot * (C::UPITCH / 4) + crow);
+    // planes [zf_lo, zf_hi) of this column have b = 0 at every point and no
+    // point outside the grid: there the update needs no sponge terms or masks
+    int zf_lo = a.nbl, zf_hi = a.nbl + a.nz;
+    {
+      const bool no_sponge = a.bscale == 0.0f;
+      const bool full = x0 + C::BX <= a.Nx && y0 + C::BY <= a.Ny;
+      const bool inner_xy = x0 >= a.nbl && x0 + C::BX <= a.nbl + a.nx && y0 >= a.nbl &&
+                            y0 + C::BY <= a.nbl + a.ny;
+      if (no_sponge) {
+        zf_lo = zbeg;
+        zf_hi = zend;
       }
-      const int aslot = ik % C::SA;
-      bad |= !mbar_wait(bar_a0 + 8 * aslot, (ik / C::SA) & 1, limit);
-
-      const float* P = ubuf + (jk % C::SU) * (C::UPITCH / 4);
-      float xr[4 * C::NROW4];
-#pragma unroll
-      for (int m = 0; m < C::NROW4; ++m) {
-        const float4 v = *reinterpret_cast<const float4*>(P + (ty + R) * C::W + 4 * tx + 4 * m);
-        xr[4 * m + 0] = v.x;
-        xr[4 * m + 1] = v.y;
-        xr[4 * m + 2] = v.z;
-        xr[4 * m + 3] = v.w;
+      if (!full || !(no_sponge || inner_xy)) {
+        zf_lo = 0;
+        zf_hi = 0;
       }
-      const int aslot_c = ik % C::SA;
-      float lap[4];
-      if (MODE == kModePerCell) {
-        // per-cell weights c_1..c_R from the staged coefficient tiles,
-        // c_0 = -2 sum_j c_j
-        float cs[4] = {0.f, 0.f, 0.f, 0.f};
+    }
+    size_t off = (static_cast<size_t>(zbeg) * a.Ny + gy) * a.pitch + gx;
+    const size_t plane_stride = static_cast<size_t>(a.Ny) * a.pitch;
+
+    // ring slots: sk holds plane jk, sn plane jn (parity pn), sa tile ik
+    int sk = R % C::SU;
+    int sn = (2 * R) % C::SU;
+    uint32_t pn = ((2 * R) / C::SU) & 1;
+    int sa = 0;
+    uint32_t pa = 0;
+
+    for (int kb = zbeg; kb < zend; kb += U) {
 #pragma unroll
-        for (int jj = 1; jj <= R; ++jj) {
-          const float4 cv = *reinterpret_cast<const float4*>(
-              cbuf + (aslot_c * NC + (jj - 1)) * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
-          const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
-          const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
+      for (int s = 0; s < U; ++s) {
+#define FD_Q(o) q[ROT ? (s + R + (o)) % NQ : (s + R + (o))]
+        const int k = kb + s;
+        if (k >= zend) break;
+        const int ik = k - zbeg;
+        const int jk = ik + R;
+        bad |= !mbar_wait(bar_u0 + 8 * sn, pn, ov.spin_limit);
+        FD_Q(R) = *reinterpret_cast<const float4*>(ubuf + sn * C::UPITCH + crow);
+        bad |= !mbar_wait(bar_a0 + 8 * sa, pa, ov.spin_limit);
+
+        const unsigned char* P = ubuf + sk * C::UPITCH + crow;
+        float xr[4 * C::NROW4];
 #pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
-            const float sy = lane(ym, l) + lane(yp, l);
-            const float sz = lane(q[R - jj], l) + lane(q[R + jj], l);
-            const float cj = lane(cv, l);
-            cs[l] += cj;
-            lap[l] = (jj == 1) ? cj * ((sx + sy) + sz) : fmaf(cj, (sx + sy) + sz, lap[l]);
+        for (int m = 0; m < C::NROW4; ++m) {
+          const float4 v = (m == C::NROW4 / 2)
+                               ? FD_Q(0)
+                               : *reinterpret_cast<const float4*>(P + 16 * (m - C::NROW4 / 2));
+          xr[4 * m + 0] = v.x;
+          xr[4 * m + 1] = v.y;
+          xr[4 * m + 2] = v.z;
+          xr[4 * m + 3] = v.w;
+        }
+        float lap[4];
+        if (MODE == kModePerCell) {
+          // per-cell weights c_1..c_R from the staged coefficient tiles,
+          // c_0 = -2 sum_j c_j
+          float cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int jj = 1; jj <= R; ++jj) {
+            const float4 cv = *reinterpret_cast<const float4*>(
+                cbuf + (sa * NC + (jj - 1)) * C::TPITCH + ctile);
+            const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
+            const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
+              const float sy = lane(ym, l) + lane(yp, l);
+              const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
+              const float cj = lane(cv, l);
+              cs[l] += cj;
+              lap[l] = (jj == 1) ? cj * ((sx + sy) + sz) : fmaf(cj, (sx + sy) + sz, lap[l]);
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) lap[l] = fmaf(-6.0f * cs[l], xr[C::RX + l], lap[l]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 4; ++l) lap[l] = c0x3 * xr[C::RX + l];
+#pragma unroll
+          for (int jj = 1; jj <= R; ++jj) {
+            const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
+            const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+            const float cj = ov.c[jj];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
+              const float sy = lane(ym, l) + lane(yp, l);
+              const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
+              lap[l] = fmaf(cj, (sx + sy) + sz, lap[l]);
+            }
           }
         }
+
+        // point sources of this plane (owner thread adds its share)
+        float src[4] = {0.f, 0.f, 0.f, 0.f};
+        if (k == iz) {
+          while (ip < iend) {
+            const InjEntry e = a.inj[ip];
+            if (e.z != k) break;
+            if (e.ly == ty && (e.lx >> 2) == tx) {
+              const float val =
+                  e.w * a.inj_val[static_cast<size_t>(a.inj_row) * a.inj_ncol + e.col];
 #pragma unroll
-        for (int l = 0; l < 4; ++l) lap[l] = fmaf(-6.0f * cs[l], xr[C::RX + l], lap[l]);
-      } else {
-#pragma unroll
-        for (int l = 0; l < 4; ++l) lap[l] = c0x3 * xr[C::RX + l];
-#pragma unroll
-        for (int jj = 1; jj <= R; ++jj) {
-          const float4 ym = *reinterpret_cast<const float4*>(P + crow - jj * C::W);
-          const float4 yp = *reinterpret_cast<const float4*>(P + crow + jj * C::W);
-          const float cj = ov.c[jj];
+              for (int l = 0; l < 4; ++l) src[l] += ((e.lx & 3) == l) ? val : 0.f;
+            }
+            ++ip;
+          }
+          iz = ip < iend ? a.inj[ip].z : INT_MAX;
+        }
+
+        const float4 up = *reinterpret_cast<const float4*>(pbuf + sa * C::TPITCH + ctile);
+        const float4 Av = *reinterpret_cast<const float4*>(abuf + sa * C::TPITCH + ctile);
+        float res[4], ev[4];
+        // the same explicit roundings in every mode and on both branches, so
+        // that a recomputed segment reproduces the stored states bit for bit
+        if (k >= zf_lo && k < zf_hi) {
+          // b = 0: (1-b) = 1 and no division; every column is inside the grid
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
-            const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
-            const float sy = lane(ym, l) + lane(yp, l);
-            const float sz = lane(q[R - jj], l) + lane(q[R + jj], l);
-            lap[l] = fmaf(cj, (sx + sy) + sz, lap[l]);
+            const float ls = __fadd_rn(lap[l], src[l]);
+            ev[l] = __fmul_rn(lane(Av, l), ls);
+            res[l] = fmaf(lane(Av, l), ls, fmaf(2.0f, lane(FD_Q(0), l), -lane(up, l)));
+          }
+        } else {
+          const int dz = sponge_depth(k, a.nbl, a.nz);
+          const float dzz = static_cast<float>(dz * dz);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float b = a.bscale * (dxx[l] + dzz);
+            const float uc = lane(FD_Q(0), l);
+            const float ls = __fadd_rn(lap[l], src[l]);
+            const float e = __fmul_rn(lane(Av, l), ls);
+            float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
+            // inside the layer divide by 1+b (fast reciprocal; select, no branch)
+            const float td = __fdividef(t, 1.0f + b);
+            t = (b != 0.0f) ? td : t;
+            res[l] = (gx + l < a.Nx) ? t : 0.0f;
+            ev[l] = (gx + l < a.Nx) ? e : 0.0f;
           }
         }
-      }
-
-      // point sources of this plane (owner thread adds its share)
-      float src[4] = {0.f, 0.f, 0.f, 0.f};
-      while (ip < iend) {
-        const InjEntry e = a.inj[ip];
-        if (e.z != k) break;
-        if (e.ly == ty && (e.lx >> 2) == tx) {
-          const float val = e.w * a.inj_val[static_cast<size_t>(a.inj_row) * a.inj_ncol + e.col];
-#pragma unroll
-          for (int l = 0; l < 4; ++l) src[l] += ((e.lx & 3) == l) ? val : 0.f;
+        if (in_grid) {
+          st_stream(out + off, res[0], res[1], res[2], res[3]);
+          if (MODE == kModeStoreE)
+            *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+          if (MODE == kModeAdjoint) {
+            const float4 ein = *reinterpret_cast<const float4*>(a.e_in + off);
+            const float4 uc = FD_Q(0);
+            float4 g = *reinterpret_cast<float4*>(a.grad + off);
+            g.x -= uc.x * ein.x * a.inv_dt2;
+            g.y -= uc.y * ein.y * a.inv_dt2;
+            g.z -= uc.z * ein.z * a.inv_dt2;
+            g.w -= uc.w * ein.w * a.inv_dt2;
+            *reinterpret_cast<float4*>(a.grad + off) = g;
+          }
         }
-        ++ip;
-      }
+        off += plane_stride;
 
-      const float4 up = *reinterpret_cast<const float4*>(pbuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
-      const float4 Av = *reinterpret_cast<const float4*>(abuf + aslot * (C::TPITCH / 4) + ty * C::BX + 4 * tx);
-      const int dz = sponge_depth(k, a.nbl, a.nz);
-      const float dzz = static_cast<float>(dz * dz);
-      float res[4], ev[4];
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const float b = a.bscale * (dxx[l] + dzz);
-        const float uc = lane(q[R], l);
-        // the same explicit roundings in every mode, so that a recomputed
-        // segment reproduces the stored states bit for bit
-        const float ls = __fadd_rn(lap[l], src[l]);
-        const float e = __fmul_rn(lane(Av, l), ls);
-        float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
-        // inside the layer divide by 1+b (fast reciprocal; select, no branch)
-        const float td = __fdividef(t, 1.0f + b);
-        t = (b != 0.0f) ? td : t;
-        res[l] = (gx + l < a.Nx) ? t : 0.0f;
-        ev[l] = (gx + l < a.Nx) ? e : 0.0f;
-      }
-      if (row_ok && col_ok) {
-        const size_t off = (static_cast<size_t>(k) * a.Ny + gy) * a.pitch + gx;
-        st_stream(out + off, res[0], res[1], res[2], res[3]);
-        if (MODE == kModeStoreE)
-          *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
-        if (MODE == kModeAdjoint) {
-          const float4 ein = *reinterpret_cast<const float4*>(a.e_in + off);
-          float4 g = *reinterpret_cast<float4*>(a.grad + off);
-          g.x -= q[R].x * ein.x * a.inv_dt2;
-          g.y -= q[R].y * ein.y * a.inv_dt2;
-          g.z -= q[R].z * ein.z * a.inv_dt2;
-          g.w -= q[R].w * ein.w * a.inv_dt2;
-          *reinterpret_cast<float4*>(a.grad + off) = g;
+        // receivers whose floor node lies in this plane: one thread each,
+        // trilinear over planes k and k+1 (both staged)
+        if (k == rz) {
+          int rq = rp;
+          while (rq < rend && a.recs[rq].z == k) ++rq;
+          const float* P0 = reinterpret_cast<const float*>(ubuf + sk * C::UPITCH);
+          const float* P1 =
+              reinterpret_cast<const float*>(ubuf + (sk + 1 == C::SU ? 0 : sk + 1) * C::UPITCH);
+          for (int e = rp + tid; e < rq; e += C::NT) {
+            const RecEntry r = a.recs[e];
+            const int o = (r.ly + R) * C::W + r.lx + C::RX;
+            const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
+            const float p0 = gy0 * (gx0 * P0[o] + r.fx * P0[o + 1]) +
+                             r.fy * (gx0 * P0[o + C::W] + r.fx * P0[o + C::W + 1]);
+            const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
+                             r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
+            a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
+                (1.0f - r.fz) * p0 + r.fz * p1;
+          }
+          rp = rq;
+          rz = rp < rend ? a.recs[rp].z : INT_MAX;
         }
-      }
 
-      // receivers whose floor node lies in this plane: one thread each,
-      // trilinear over planes k and k+1 (both staged)
-      {
-        int rq = rp;
-        while (rq < rend && a.recs[rq].z == k) ++rq;
-        const float* P1 = ubuf + ((jk + 1) % C::SU) * (C::UPITCH / 4);
-        for (int e = rp + tid; e < rq; e += C::NT) {
-          const RecEntry r = a.recs[e];
-          const int o = (r.ly + R) * C::W + r.lx + C::RX;
-          const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
-          const float p0 = gy0 * (gx0 * P[o] + r.fx * P[o + 1]) +
-                           r.fy * (gx0 * P[o + C::W] + r.fx * P[o + C::W + 1]);
-          const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
-                           r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
-          a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
-              (1.0f - r.fz) * p0 + r.fz * p1;
+        if (__syncthreads_or(bad)) goto fail;
+        if (tid == 0) {
+          issue_u(jk + C::SU, sk * C::UPITCH);
+          issue_a(ik + C::SA, sa * C::TPITCH);
         }
-        rp = rq;
+        sk = (sk + 1 == C::SU) ? 0 : sk + 1;
+        sn = (sn + 1 == C::SU) ? 0 : sn + 1;
+        pn ^= (sn == 0) ? 1u : 0u;
+        sa = (sa + 1 == C::SA) ? 0 : sa + 1;
+        pa ^= (sa == 0) ? 1u : 0u;
+#undef FD_Q
       }
-
-      if (__syncthreads_or(bad)) goto fail;
-      if (tid == 0) {
-        issue_u(jk + C::SU);
-        issue_a(ik + C::SA);
-      }
+      if (!ROT) {
 #pragma unroll
-      for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + U];
+      }
     }
   }
   // every issued copy has been waited for; release the barriers so the
@@ -445,10 +527,10 @@ fail:
     // wait (bounded) for every copy this CTA still has in flight
     for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
       if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
-      mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, limit);
+      mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, ov.spin_limit);
     }
     for (int i = max(0, ia_next - C::SA); i < ia_next; ++i)
-      mbar_wait(bar_a0 + 8 * (i % C::SA), (i / C::SA) & 1, limit);
+      mbar_wait(bar_a0 + 8 * (i % C::SA), (i / C::SA) & 1, ov.spin_limit);
   }
 }
 

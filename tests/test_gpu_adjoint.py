@@ -120,3 +120,24 @@ def test_directional_derivative_by_central_differences_on_gpu(fd):
     fd_dir = (losses[0] - losses[1]) / (2 * eps)
     ad_dir = float(np.sum(grad.astype(np.float64) * dm))
     assert abs(fd_dir - ad_dir) <= 2e-2 * abs(ad_dir), (fd_dir, ad_dir)
+
+
+def test_autograd_function_gives_the_oracle_gradient(fd):
+    """loss = 0.5 ||F(m) - d||^2 through torch.autograd: the backward pass of
+    AcousticModelling (fd_backward) against the FP64 oracle gradient."""
+    import torch
+    from paper_2312_13094_gb300.autograd import modelling
+    w = problem(8, nt=45)
+    d_obs = observed(w)
+    m64 = 1.0 / w["v"].astype(np.float64) ** 2
+    m = torch.tensor(m64.astype(np.float32), device="cuda", requires_grad=True)
+    d = torch.tensor(d_obs, device="cuda")
+    with fd.Grid.from_workload(w) as g:
+        rec = modelling(m, g, w["src"], w["wavelet"], w["rec"], n_checkpoints=5)
+        loss = 0.5 * ((rec - d) ** 2).sum()
+        loss.backward()
+    ref, rloss, _ = oracle.adjoint_gradient(og_of(w), m64, w["nt"], w["src"], w["wavelet"],
+                                            w["rec"], d_obs=d_obs.astype(np.float64))
+    assert abs(float(loss) - rloss) <= 1e-5 * abs(rloss)
+    grad = m.grad.cpu().numpy()
+    assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) <= 1e-4
