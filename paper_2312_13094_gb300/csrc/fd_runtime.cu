@@ -199,11 +199,12 @@ const TileShape kShapes[kNumShapes] = {
 // L2.  Lockstep columns land on the SMs as evenly as the block scheduler can
 // place them, so the slowest SM holds ceil(T / SMs) columns: among the
 // lockstep shapes the one with the fewest tile points on that SM wins, then
-// the wider tile, then the taller one.  Without a lockstep shape the widest
-// (then tallest) tile runs the equal-share sweep, whose shares are balanced by
-// construction.  Measured on GB300 (SO 8, Gpts/s): 592^3 lockstep 64x8 283,
-// 32x16 275, 128x8 256, 32x8 250, 64x16 245; 768^3 sweep 128x8 255, 64x16
-// 228, 64x8 203, 32x16 183, 32x8 148.
+// the wider tile, then the taller one.  Without a lockstep shape, the shape
+// with the most resident warps (then the widest, then the tallest) runs the
+// equal-share sweep, whose shares are balanced by construction.  Measured on
+// GB300 (Gpts/s): SO 8 592^3 lockstep 64x8 283, 32x16 275, 128x8 256, 32x8
+// 250, 64x16 245; SO 8 768^3 sweep 128x8 255, 64x16 228, 64x8 203, 32x16 183,
+// 32x8 148; SO 16 592^3 sweep 32x16 (12 warps per SM) 156, 128x8 (8) 145.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
   (void)Nz;
   int dev = 0, sms = 0;
@@ -213,14 +214,19 @@ TileShape default_shape(int R, int Nx, int Ny, int Nz) {
   auto wider = [](const TileShape& p, const TileShape& q) {  // p before q
     return p.tx != q.tx ? p.tx > q.tx : p.ty > q.ty;
   };
-  int best = -1, best_sweep = 0;
-  long long best_load = 0;
+  int best = -1, best_sweep = -1;
+  long long best_load = 0, best_warps = 0;
   for (int i = 0; i < kNumShapes; ++i) {
     const TileShape& t = kShapes[i];
     const int bx = 4 * t.tx, by = t.ty;
     const long long T = (long long)((Nx + bx - 1) / bx) * ((Ny + by - 1) / by);
     const long long slots = sweep_ctas(R, t, kModeForward);
-    if (wider(t, kShapes[best_sweep])) best_sweep = i;
+    const long long warps = slots * (t.tx * t.ty / 32);
+    if (best_sweep < 0 || warps > best_warps ||
+        (warps == best_warps && wider(t, kShapes[best_sweep]))) {
+      best_sweep = i;
+      best_warps = warps;
+    }
     if (T <= slots && 2 * T >= slots) {
       const long long load = (T + sms - 1) / sms * (long long)(bx * by);
       if (best < 0 || load < best_load || (load == best_load && wider(t, kShapes[best]))) {
