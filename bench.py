@@ -446,18 +446,32 @@ def run_learned(args):
     t1 = time.time()
     l1 = net.train(S, epochs=args.epochs, batch=65536, lr=1e-3)
     t_train = time.time() - t1
-    rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt)
+    rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt,
+                       ladder=args.ladder)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     np.save(os.path.join(ROOT, "gpurun_out", "learned_params.npy"), net.params())
-    plain = float(np.mean([r["plain"] for r in rows]))
-    learned = float(np.mean([r["learned"] for r in rows]))
+
+    def mean(key):
+        return float(np.mean([r[key] for r in rows]))
+
+    ladder = {}
+    if args.ladder:
+        for (hh, so, _) in lr.LADDER:
+            key = f"h{hh:.4g}_so{so}"
+            ladder[key] = {"rel_l2": mean(key), "ms": mean("ms_" + key)}
+    plain = mean("plain")
+    learned = mean("learned_table")
     print(json.dumps({
-        "metric": "receiver rel. L2 vs fine SO16 (learned coarse)", "value": learned,
-        "unit": "rel. L2", "higher_is_better": False, "plain_coarse": plain,
-        "plain_coarse_so16": float(np.mean([r["plain16"] for r in rows])),
-        "ms_coarse_plain_so16": float(np.mean([r["ms_plain16"] for r in rows])),
-        "ms_fine": float(np.mean([r["ms_fine"] for r in rows])),
-        "ms_coarse_plain": float(np.mean([r["ms_plain"] for r in rows])),
-        "ms_coarse_learned": float(np.mean([r["ms_learned"] for r in rows])),
+        "metric": "receiver rel. L2 vs fine SO16 (learned coarse, weight table)",
+        "value": learned, "unit": "rel. L2", "higher_is_better": False,
+        "plain_coarse": plain, "learned_percell": mean("learned"),
+        "plain_coarse_so16": mean("plain16"),
+        "ms_coarse_plain_so16": mean("ms_plain16"),
+        "ms_fine": mean("ms_fine"),
+        "ms_coarse_plain": mean("ms_plain"),
+        "ms_coarse_learned_percell": mean("ms_learned"),
+        "ms_coarse_learned": mean("ms_learned_table"),
+        "plain_ladder": ladder,
         "loss_before": l0, "loss_after": l1, "samples": int(S.shape[0]),
         "train_models": args.train_models, "test_models": args.test_models,
         "epochs": args.epochs, "data_s": t_data, "train_s": t_train, "rows": rows,
@@ -469,9 +483,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "adjoint", "batched", "learned"])
-    ap.add_argument("--train-models", type=int, default=48)
-    ap.add_argument("--test-models", type=int, default=8)
+    ap.add_argument("--train-models", type=int, default=200)
+    ap.add_argument("--test-models", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--ladder", action="store_true",
+                    help="learned workload: also time plain SO 8/16 at h 16 and 12.8 m")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -225,6 +225,19 @@ fd_status fd_mlp_coefficients(fd_mlp net, int64_t n, const float* features, floa
 /* per-cell weights of every cell of a space-order-8 grid from its model,
  * computed by the network on the device (call after fd_set_model) */
 fd_status fd_set_learned_coefficients(fd_grid grid, fd_mlp net, double f_hz);
+/* The same weights without per-cell fields: for fixed h, dt and f the
+ * network's input varies only with the Courant number C = v dt / h, so the
+ * network is evaluated (on the device) at `nodes` values A_i evenly spaced
+ * from (v_min dt/h)^2 to (v_max dt/h)^2 of the current model (input
+ * C_i = sqrt(A_i)), and each point of every step takes c_1..c_4 interpolated
+ * linearly in A between the two nodes around its own A = dt^2 v^2 / h^2
+ * (clamped to the end nodes).  The step then moves the 16 bytes per point of
+ * the plain stencil instead of 32.  The
+ * table is rebuilt by the next call, and dropped by fd_set_coefficients or
+ * fd_set_learned_coefficients; call again after fd_set_model.
+ * Errors: FD_ERR_ARG (null, space order not 8, nodes outside [2, 256]),
+ * FD_ERR_STATE (no model), FD_ERR_CUDA. */
+fd_status fd_set_learned_table(fd_grid grid, fd_mlp net, double f_hz, int32_t nodes);
 /* Training-data helpers.  fd_sample_stencil writes, for each padded cell
  * (x, y, z) of cells[n][3], the current wavefield at the cell and at
  * distances j*stride (j = 1..radius) along -x, +x, -y, +y, -z, +z:

@@ -135,3 +135,25 @@ def features(v_kms, h, dt, f_hz):
     x[..., 2] = dt / 1.0
     x[..., 3] = f_hz / 10.0
     return x
+
+
+def table_coefficients(theta, courant, h, dt, f_hz, nodes, lo, hi, c_taylor):
+    """Weights c_1..c_4 [..., 4] of points with Courant numbers `courant`
+    (v dt / h, any shape) when the network is evaluated only at `nodes`
+    values of A = C^2 evenly spaced from lo^2 to hi^2 (the network sees
+    C_i = sqrt(A_i)) and interpolated linearly in A in between, clamped to the
+    end nodes: the definition of the table mode.  With hi == lo every point
+    takes the first node."""
+    A = np.asarray(courant, np.float64) ** 2
+    alo, ahi = lo * lo, hi * hi
+    Ai = alo + (ahi - alo) * np.arange(nodes, dtype=np.float64) / (nodes - 1)
+    X = np.stack([np.sqrt(Ai), np.full(nodes, h / 10.0), np.full(nodes, dt / 1.0),
+                  np.full(nodes, f_hz / 10.0)], axis=1)
+    T = coefficients(theta, X, c_taylor)                      # [nodes, 4]
+    if ahi > alo:
+        x = np.clip((A - alo) * ((nodes - 1) / (ahi - alo)), 0.0, nodes - 1)
+    else:
+        x = np.zeros_like(A)
+    i = np.minimum(np.floor(x).astype(np.int64), nodes - 2)
+    f = (x - i)[..., None]
+    return T[i] + f * (T[i + 1] - T[i])

@@ -83,6 +83,7 @@ _SIGS = {
     "fd_batch_forward": (_S, [ctypes.c_int32, ctypes.POINTER(fd_shot), ctypes.c_int32]),
     "fd_set_coefficients": (_S, [_G, _P, ctypes.c_int32]),
     "fd_set_learned_coefficients": (_S, [_G, _G, ctypes.c_double]),
+    "fd_set_learned_table": (_S, [_G, _G, ctypes.c_double, ctypes.c_int32]),
     "fd_mlp_create": (_S, [ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "fd_mlp_destroy": (_S, [_G]),
     "fd_mlp_get_params": (_S, [_G, _P]),

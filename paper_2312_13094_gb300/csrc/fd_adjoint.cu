@@ -49,7 +49,7 @@ fd_status adjoint_impl(fd_grid g, const fd_points* src, const float* wavelet,
                        const fd_points* rec, const float* d_obs, const float* resid_in,
                        int32_t n_checkpoints, float* grad_m, double* loss_out) {
   if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
-  if (g->percell)
+  if (g->percell || g->table_mode)
     return fail(FD_ERR_STATE, "the adjoint is built for the symmetric uniform-weight stencil");
   const int nt = g->d.nt;
   const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;

@@ -226,7 +226,8 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
     fd_grid g = shots[i].grid;
     if (!g) return fail(FD_ERR_ARG, "shot %d has no grid", i);
     if (!g->model_set) return fail(FD_ERR_STATE, "shot %d has no model", i);
-    if (g->percell) return fail(FD_ERR_STATE, "shot %d uses per-cell weights", i);
+    if (g->percell || g->table_mode)
+      return fail(FD_ERR_STATE, "shot %d uses per-cell weights", i);
     for (int j = 0; j <= g->R && j <= g0->R; ++j)
       if (g->c[j] != g0->c[j]) return fail(FD_ERR_ARG, "shots must share stencil weights");
     if (g->d.device != g0->d.device || g->R != g0->R || g->d.nt != g0->d.nt)

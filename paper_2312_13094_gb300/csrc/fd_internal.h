@@ -8,6 +8,7 @@
 namespace fd {
 
 constexpr int kMaxR = 8;  // space order up to 16
+constexpr int kTableNodes = 256;  // largest weight table of kModeTable
 
 // One source node: padded z, tile-local x/y of the node, scaled weight and the
 // column of the value table (wavelet or residual) that feeds it.
@@ -31,7 +32,9 @@ enum StepMode : int {
   kModeForward = 0,    // u^{n+1} only
   kModeStoreE = 1,     // also e = (dt^2/m)(L u + s) for the imaging condition
   kModeAdjoint = 2,    // also grad -= u_cur * e_in / dt^2 (u_cur = z^{n+1})
-  kModePerCell = 3     // forward with per-cell weights c_1..c_R (space order 8)
+  kModePerCell = 3,    // forward with per-cell weights c_1..c_R (space order 8)
+  kModeTable = 4       // forward with weights c_1..c_4 interpolated per point from a
+                       // table over A = (v dt / h)^2 (space order 8)
 };
 
 // Everything one launch of the step kernel needs besides the tensor maps.
@@ -56,6 +59,10 @@ struct StepArgs {
   float* e_out;              // kModeStoreE
   const float* e_in;         // kModeAdjoint
   float* grad;               // kModeAdjoint (padded, pitched)
+  const float4* table;       // kModeTable: per node i, c_1..c_4 at node i and the
+                             // step to node i + 1 (2 float4 per node)
+  float tab_lo, tab_inv;     // node i sits at A = tab_lo + i / tab_inv (tab_inv 0: one)
+  int32_t tab_nodes;
   float inv_dt2;
   int32_t* err;              // device error word (bit 0: wait timed out)
   long long spin_limit;      // clock cycles before a wait gives up

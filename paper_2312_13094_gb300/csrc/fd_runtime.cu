@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -191,22 +192,27 @@ int sweep_ctas(int R, const TileShape& t, int mode) {
   return std::max(1, per) * std::max(1, sms);
 }
 
+int lockstep_ctas(int R, const TileShape& t, int mode, long long columns) {
+  const int slots = sweep_ctas(R, t, mode);
+  if (t.ctas > 0 || columns <= 0 || columns > slots) return slots;
+  return int(columns * (slots / columns));
+}
+
 const TileShape kShapes[kNumShapes] = {
     {16, 16, 2, 0}, {32, 8, 2, 0}, {8, 16, 1, 0}, {16, 8, 2, 0}, {8, 8, 1, 0}};
 
-// Default tile.  A shape whose columns can all be resident at once (and fill
-// at least half of the slots) runs as lockstep columns that share halos in
-// L2.  Lockstep columns land on the SMs as evenly as the block scheduler can
-// place them, so the slowest SM holds ceil(T / SMs) columns: among the
-// lockstep shapes the one with the fewest tile points on that SM wins, then
-// the wider tile, then the taller one.  Without a lockstep shape, the shape
+// Default tile.  A shape whose T columns can all be resident at once runs in
+// lockstep (k = slots / T z chunks per column, all in step), sharing halos in
+// L2.  The k T chunks land on the SMs as evenly as the block scheduler can
+// place them, so the slowest SM holds ceil(k T / SMs) chunks: among the
+// lockstep shapes the one with the fewest points on that SM wins, then the
+// wider tile, then the taller one.  Without a lockstep shape, the shape
 // with the most resident warps (then the widest, then the tallest) runs the
 // equal-share sweep, whose shares are balanced by construction.  Measured on
 // GB300 (Gpts/s): SO 8 592^3 lockstep 64x8 283, 32x16 275, 128x8 256, 32x8
 // 250, 64x16 245; SO 8 768^3 sweep 128x8 255, 64x16 228, 64x8 203, 32x16 183,
 // 32x8 148; SO 16 592^3 sweep 32x16 (12 warps per SM) 156, 128x8 (8) 145.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
-  (void)Nz;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -227,8 +233,11 @@ TileShape default_shape(int R, int Nx, int Ny, int Nz) {
       best_sweep = i;
       best_warps = warps;
     }
-    if (T <= slots && 2 * T >= slots) {
-      const long long load = (T + sms - 1) / sms * (long long)(bx * by);
+    if (T <= slots) {
+      // k chunks of Nz / k planes per column; the busiest SM holds
+      // ceil(k T / SMs) chunks
+      const long long k = slots / T;
+      const long long load = (k * T + sms - 1) / sms * (long long)(bx * by) * Nz / k;
       if (best < 0 || load < best_load || (load == best_load && wider(t, kShapes[best]))) {
         best = i;
         best_load = load;
@@ -459,7 +468,17 @@ StepArgs base_args(fd_grid g) {
   a.err = g->d_err;
   a.spin_limit = g->spin_limit;
   a.debug_skip_plane = -1;
+  a.table = g->table;
+  a.tab_lo = g->tab_lo;
+  a.tab_inv = g->tab_inv;
+  a.tab_nodes = g->tab_nodes;
   return a;
+}
+
+int forward_mode(fd_grid g) {
+  if (g->percell) return kModePerCell;
+  if (g->table_mode) return kModeTable;
+  return kModeForward;
 }
 
 // Host image of the sweep descriptor of one run (grid, field pair, tables).
@@ -495,14 +514,13 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   if (rs.nsteps <= 0) return FD_OK;
   cudaError_t e;
   Fields& F = *rs.f;
-  const int mode = (g->percell && rs.mode == kModeForward) ? int(kModePerCell) : rs.mode;
-  // one whole column per CTA when the columns fill at least half of the
-  // resident slots: every CTA then walks z in step with its neighbours, which
-  // share halos in L2; otherwise equal contiguous shares of all the
-  // (tile, plane) units over every resident slot
-  int G = sweep_ctas(g->R, g->shape, mode);
-  const long long T = (long long)g->tiles_x * g->tiles_y;
-  if (g->shape.ctas == 0 && T < G && 2 * T >= G) G = int(T);
+  const int mode = rs.mode == kModeForward ? forward_mode(g) : rs.mode;
+  // lockstep when all columns fit in the resident slots: k = slots / T CTAs
+  // per column, each taking one of k equal z chunks (the shares below then
+  // fall on chunk boundaries), so every CTA walks z in step with its
+  // neighbours, which share halos in L2; otherwise equal contiguous shares
+  // of all the (tile, plane) units over every resident slot
+  int G = lockstep_ctas(g->R, g->shape, mode, (long long)g->tiles_x * g->tiles_y);
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
   struct {
@@ -763,6 +781,7 @@ fd_status fd_destroy_grid(fd_grid g) {
   }
   if (g->A) cudaFree(g->A);
   if (g->coef) cudaFree(g->coef);
+  if (g->table) cudaFree(g->table);
   if (g->d_err) cudaFree(g->d_err);
   for (DevBuf* b : {&g->tab.inj_start, &g->tab.inj, &g->tab.rec_start, &g->tab.recs,
                     &g->tab_adj.inj_start, &g->tab_adj.inj, &g->tab_adj.rec_start,
@@ -804,6 +823,7 @@ fd_status fd_set_model(fd_grid g, const float* data, int32_t kind) {
   e = model_to_A(dev, kind, g->d.nx, g->d.ny, g->d.nz, g->d.nbl, g->Nx, g->Ny, g->Nz,
                  g->pitch, g->d.dt * g->d.dt / (g->d.h * g->d.h), g->A, g->stream);
   if (e) return cuda_fail(e, "model set-up");
+  g->vmin = vmin;
   g->vmax = vmax;
   if (g->d.nbl > 0) {
     const double gmax = 3.0 * double(vmax) * log(1000.0) / (2.0 * g->d.nbl * g->d.h);
@@ -942,7 +962,7 @@ fd_status fd_get_info(fd_grid g, fd_grid_info* info) {
   info->pitch = g->pitch;
   info->tile_x = 4 * g->shape.tx;
   info->tile_y = g->shape.ty;
-  info->ctas = sweep_ctas(g->R, g->shape, g->percell ? int(kModePerCell) : int(kModeForward));
+  info->ctas = sweep_ctas(g->R, g->shape, forward_mode(g));
   info->v_max = g->vmax;
   info->cfl_limit = g->cfl;
   info->launches = g_launches.load();
@@ -963,6 +983,7 @@ fd_status fd_set_coefficients(fd_grid g, const float* c, int32_t mode) {
   if (!g) return fail(FD_ERR_ARG, "null grid");
   cudaSetDevice(g->d.device);
   g->graph_valid = false;
+  g->table_mode = false;
   if (mode == FD_COEF_TAYLOR) {
     fd_weights(g->R, g->c);
     g->percell = false;
@@ -1006,6 +1027,54 @@ fd_status fd_set_learned_coefficients(fd_grid g, fd_mlp net, double f_hz) {
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e) return cuda_fail(e, "learned coefficients");
   g->percell = true;
+  g->table_mode = false;
+  g->graph_valid = false;
+  return FD_OK;
+}
+
+fd_status fd_set_learned_table(fd_grid g, fd_mlp net, double f_hz, int32_t nodes) {
+  clear_error();
+  if (!g || !net) return fail(FD_ERR_ARG, "null argument");
+  if (g->R != 4) return fail(FD_ERR_ARG, "the network predicts space-order-8 weights");
+  if (nodes < 2 || nodes > kTableNodes)
+    return fail(FD_ERR_ARG, "table nodes must be in [2, %d]", kTableNodes);
+  if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
+  cudaSetDevice(g->d.device);
+  if (!g->table) {
+    cudaError_t e =
+        dev_alloc(reinterpret_cast<void**>(&g->table), 2 * kTableNodes * sizeof(float4));
+    if (e) return cuda_fail(e, "table allocation");
+  }
+  // nodes evenly spaced in A = C^2 over the model's Courant numbers
+  // C = v dt / h; the network sees C_i = sqrt(A_i)
+  const double clo = g->vmin * g->d.dt / g->d.h, chi = g->vmax * g->d.dt / g->d.h;
+  const double alo = clo * clo, ahi = chi * chi;
+  std::vector<float> feat(size_t(nodes) * 4), coef(size_t(nodes) * 4);
+  for (int i = 0; i < nodes; ++i) {
+    feat[4 * i + 0] = float(std::sqrt(alo + (ahi - alo) * i / (nodes - 1)));
+    feat[4 * i + 1] = float(g->d.h / 10.0);
+    feat[4 * i + 2] = float(g->d.dt / 1.0);
+    feat[4 * i + 3] = float(f_hz / 10.0);
+  }
+  fd_status st = fd_mlp_coefficients(net, nodes, feat.data(), coef.data());
+  if (st) return st;
+  // per node: the weights and the step to the next node (zero at the last)
+  std::vector<float> tab(size_t(nodes) * 8);
+  for (int i = 0; i < nodes; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      tab[8 * i + j] = coef[4 * i + j];
+      tab[8 * i + 4 + j] = i + 1 < nodes ? coef[4 * (i + 1) + j] - coef[4 * i + j] : 0.0f;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g->table, tab.data(), tab.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, g->stream);
+  if (!e) e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_fail(e, "table upload");
+  g->tab_nodes = nodes;
+  g->tab_lo = float(alo);
+  g->tab_inv = ahi > alo ? float((nodes - 1) / (ahi - alo)) : 0.0f;
+  g->table_mode = true;
+  g->percell = false;
   g->graph_valid = false;
   return FD_OK;
 }

@@ -86,8 +86,13 @@ struct fd_grid_s {
   float* coef = nullptr;   // per-cell weights c_1..c_R, field j at coef + j*ncell
   CUtensorMap mapC;
   bool percell = false;
+  // kModeTable: c_1..c_4 at tab_nodes Courant numbers tab_lo + i / tab_inv
+  float4* table = nullptr;
+  int tab_nodes = 0;
+  float tab_lo = 0.0f, tab_inv = 0.0f;
+  bool table_mode = false;
   bool model_set = false;
-  double vmax = 0.0;
+  double vmin = 0.0, vmax = 0.0;
   float bscale = 0.0f;
   double c[fd::kMaxR + 1] = {};
   double cfl = 0.0;
@@ -125,8 +130,12 @@ cudaError_t launch_sweep(int R, const TileShape& t, int mode, const ShotDesc* sh
                          const long long* prefix, int nshots, const StepOverride& ov, int grid,
                          cudaStream_t s);
 int sweep_ctas(int R, const TileShape& t, int mode);
+// CTAs of one step launch: k = slots / columns per column when the columns fit
+// in the resident slots (lockstep z chunks), else every resident slot
+int lockstep_ctas(int R, const TileShape& t, int mode, long long columns);
 void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d);
 StepArgs base_args(fd_grid g);
+int forward_mode(fd_grid g);  // kModeForward, kModePerCell or kModeTable
 fd_status upload_tables(fd_grid g, const fd_points* src, double src_scale,
                         const fd_points* rec, Tables& t);
 fd_status build_injection(fd_grid g, const fd_points* pts, double scale,

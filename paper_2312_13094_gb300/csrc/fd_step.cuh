@@ -55,22 +55,27 @@ struct Cfg {
   static_assert(W <= 256 && H <= 256, "TMA box too large");
 };
 
-// Threads per SM that the launch bounds aim for: the register queue of the
-// wide stencils (2R+1 float4 per thread) needs more registers per thread.
-constexpr int threads_per_sm(int R) { return R <= 4 ? 768 : 512; }
+// Threads per SM that the launch bounds aim for.  SO <= 8: 640, five
+// 128-thread CTAs with 96 registers each (no spills) and room for a 2-plane
+// prefetch on the 64x8 tile; six CTAs at 80 registers with a 1-plane prefetch
+// measured 282 against 293 Gpts/s on 592^3.  The wider stencils need more
+// registers for their register queue (2R+1 float4 per thread): 512.
+constexpr int threads_per_sm(int R, int /*MODE*/ = kModeForward) { return R <= 4 ? 640 : 512; }
 
-// Planes per unrolled block of the z loop (see run_column).  One: on GB300
-// the 9-plane rotating body of SO 8 overflowed the instruction cache (234 vs
-// 280 Gpts/s on 592^3) and two planes per block ran 1.5 % slower than one.
-constexpr int zloop_unroll(int) { return 1; }
+// Static shared memory of a mode beyond the rings (the weight table).
+constexpr uint32_t static_smem(int MODE) {
+  return MODE == kModeTable ? 2u * kTableNodes * 16u : 0u;
+}
+
 
 // Prefetch depth of a tile shape: the deepest ring (1..6 planes beyond the
 // R+1 in use) whose shared memory still lets the CTAs that the launch bounds
-// admit be resident together (768 threads per SM for R <= 4: three CTAs of
-// 256 threads, six of 128 or twelve of 64; 512 for the wider stencils).
-template <int R, int TX, int TY, int NC>
+// admit be resident together (640 threads per SM for R <= 4: two CTAs of
+// 256 threads, five of 128 or ten of 64; 512 for the wider stencils).
+template <int R, int TX, int TY, int NC, int MODE = kModeForward>
 constexpr int auto_pf() {
-  const uint32_t budget = 219u * 1024u / (threads_per_sm(R) / (TX * TY));
+  const uint32_t budget =
+      219u * 1024u / (threads_per_sm(R, MODE) / (TX * TY)) - static_smem(MODE);
   const int rx = ((R + 3) / 4) * 4;
   const uint32_t up = ((4 * TX + 2 * rx) * (TY + 2 * R) * 4 + 127) / 128 * 128;
   const uint32_t tp = (4 * TX * TY * 4 + 127) / 128 * 128;
@@ -186,10 +191,11 @@ __device__ __forceinline__ float lane(const float4& v, int i) {
 // jk mod SU with plane jk + SU and slot i mod SA with tile i + SA.  The slots
 // are tracked as byte offsets that advance by one pitch per plane.
 //
-// The z loop runs in blocks of U planes (zloop_unroll).  With U = 2R+1 the
-// queue rotates by register naming: plane jk + o sits in q[(s + R + o) mod
-// (2R+1)] at unrolled position s.  Otherwise the queue holds 2R+U entries,
-// plane jk + o sits in q[s + R + o], and the queue shifts by U after a block.
+// Register queue: q[R + o] holds the thread's own float4 of plane jk + o,
+// o = -R .. R; it shifts by one entry per plane.  (Unrolling the z loop by
+// 2R+1 so that the queue rotates by register naming instead was measured
+// slower on GB300: the SO 8 body then overflows the instruction cache, 234
+// against 280 Gpts/s on 592^3; two planes per block ran 1.5 % slower.)
 template <int R, int TX, int TY, int PF, int MODE>
 __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            const CUtensorMap* tm_prev,
@@ -202,9 +208,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
   constexpr int NQ = 2 * R + 1;
-  constexpr int U = zloop_unroll(R);
-  constexpr bool ROT = (U == NQ);
-  constexpr int QN = ROT ? NQ : NQ + U - 1;
   constexpr uint32_t URING = C::SU * C::UPITCH;
   constexpr uint32_t ARING = C::SA * C::TPITCH;
   const int tid = threadIdx.x;
@@ -231,6 +234,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const unsigned char* abuf = smem + C::OFF_A;
   const unsigned char* cbuf = smem + C::OFF_C;
 
+  // kModeTable: the weight table of this grid, read from every point's
+  // Courant number (made visible by the barrier below)
+  __shared__ float4 s_tab[MODE == kModeTable ? 2 * kTableNodes : 1];
+  if (MODE == kModeTable) {
+    for (int i = tid; i < 2 * a.tab_nodes; i += C::NT) s_tab[i] = a.table[i];
+  }
   if (tid == 0) {
     for (int s = 0; s < C::SU; ++s) mbar_init(bar_u0 + 8 * s, 1);
     for (int s = 0; s < C::SA; ++s) mbar_init(bar_a0 + 8 * s, 1);
@@ -271,7 +280,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   // byte offsets of the thread's own float4 in a staged plane / tile
   const uint32_t crow = 4u * ((ty + R) * C::W + 4 * tx + C::RX);
   const uint32_t ctile = 4u * (ty * C::BX + 4 * tx);
-  float4 q[QN];
+  float4 q[NQ];
   bool bad = false;
 
 #pragma unroll
@@ -342,12 +351,9 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     int sa = 0;
     uint32_t pa = 0;
 
-    for (int kb = zbeg; kb < zend; kb += U) {
-#pragma unroll
-      for (int s = 0; s < U; ++s) {
-#define FD_Q(o) q[ROT ? (s + R + (o)) % NQ : (s + R + (o))]
-        const int k = kb + s;
-        if (k >= zend) break;
+    for (int k = zbeg; k < zend; ++k) {
+      {
+#define FD_Q(o) q[R + (o)]
         const int ik = k - zbeg;
         const int jk = ik + R;
         bad |= !mbar_wait(bar_u0 + 8 * sn, pn, ov.spin_limit);
@@ -367,14 +373,33 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           xr[4 * m + 3] = v.w;
         }
         float lap[4];
-        if (MODE == kModePerCell) {
-          // per-cell weights c_1..c_R from the staged coefficient tiles,
-          // c_0 = -2 sum_j c_j
+        if (MODE == kModePerCell || MODE == kModeTable) {
+          // per-point weights c_1..c_R, c_0 = -2 sum_j c_j: from the staged
+          // coefficient tiles, or interpolated linearly in the table at the
+          // point's own A = (v dt / h)^2
+          float ct[4][R];
+          if (MODE == kModeTable) {
+            const float4 At = *reinterpret_cast<const float4*>(abuf + sa * C::TPITCH + ctile);
+            const float top = static_cast<float>(a.tab_nodes - 1);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const float x = fminf(fmaxf((lane(At, l) - a.tab_lo) * a.tab_inv, 0.0f), top);
+              const int i = min(static_cast<int>(x), a.tab_nodes - 2);
+              const float f = x - static_cast<float>(i);
+              const float4 t0 = s_tab[2 * i];
+              const float4 dt = s_tab[2 * i + 1];
+#pragma unroll
+              for (int jj = 1; jj <= R; ++jj)
+                ct[l][jj - 1] = fmaf(f, lane(dt, jj - 1), lane(t0, jj - 1));
+            }
+          }
           float cs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int jj = 1; jj <= R; ++jj) {
-            const float4 cv = *reinterpret_cast<const float4*>(
-                cbuf + (sa * NC + (jj - 1)) * C::TPITCH + ctile);
+            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (MODE == kModePerCell)
+              cv = *reinterpret_cast<const float4*>(cbuf + (sa * NC + (jj - 1)) * C::TPITCH +
+                                                    ctile);
             const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
             const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
 #pragma unroll
@@ -382,7 +407,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
               const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
               const float sy = lane(ym, l) + lane(yp, l);
               const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
-              const float cj = lane(cv, l);
+              const float cj = (MODE == kModeTable) ? ct[l][jj - 1] : lane(cv, l);
               cs[l] += cj;
               lap[l] = (jj == 1) ? cj * ((sx + sy) + sz) : fmaf(cj, (sx + sy) + sz, lap[l]);
             }
@@ -504,11 +529,9 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         pn ^= (sn == 0) ? 1u : 0u;
         sa = (sa + 1 == C::SA) ? 0 : sa + 1;
         pa ^= (sa == 0) ? 1u : 0u;
-#undef FD_Q
-      }
-      if (!ROT) {
 #pragma unroll
-        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + U];
+        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+#undef FD_Q
       }
     }
   }
@@ -541,7 +564,7 @@ fail:
 // the number of resident CTAs every SM streams the same number of planes and
 // no CTA waits for a second wave.
 template <int R, int TX, int TY, int PF, int MODE>
-__global__ void __launch_bounds__(TX* TY, threads_per_sm(R) / (TX * TY))
+__global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
     sweep_kernel(const ShotDesc* __restrict__ shots, const long long* __restrict__ prefix,
                  int nshots, const __grid_constant__ StepOverride ov) {
   extern __shared__ unsigned char smem_raw[];

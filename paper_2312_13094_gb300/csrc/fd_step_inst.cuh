@@ -10,7 +10,7 @@ namespace {
 
 template <int R, int TX, int TY, int MODE>
 constexpr int pf_of() {
-  return auto_pf<R, TX, TY, MODE == kModePerCell ? R : 0>();
+  return auto_pf<R, TX, TY, MODE == kModePerCell ? R : 0, MODE>();
 }
 
 template <int R, int TX, int TY, int PF, int MODE>
@@ -59,13 +59,27 @@ int occupancy_one() {
 // depth of each follows from its shared-memory budget (auto_pf).
 #define FD_FOR_EACH_SHAPE(X) X(16, 16) X(32, 8) X(8, 16) X(16, 8) X(8, 8)
 
+// Per-cell and table weights exist for space order 8 only; other radii map
+// those modes to the plain forward kernel (the runtime never asks for them).
 #if FD_R == 4
-#define FD_PERCELL(F, TX, TY) \
-  case kModePerCell: return F<FD_R, TX, TY, pf_of<FD_R, TX, TY, 3>(), 3>
+#define FD_MODE_PERCELL 3
+#define FD_MODE_TABLE 4
 #else
-#define FD_PERCELL(F, TX, TY) \
-  case kModePerCell: return F<FD_R, TX, TY, pf_of<FD_R, TX, TY, 0>(), 0>
+#define FD_MODE_PERCELL 0
+#define FD_MODE_TABLE 0
 #endif
+#define FD_PERCELL_LAUNCH(TX, TY)                                                          \
+  case kModePerCell:                                                                       \
+    return launch_one<FD_R, TX, TY, pf_of<FD_R, TX, TY, FD_MODE_PERCELL>(), FD_MODE_PERCELL>( \
+        shots, prefix, nshots, ov, grid, s);                                               \
+  case kModeTable:                                                                         \
+    return launch_one<FD_R, TX, TY, pf_of<FD_R, TX, TY, FD_MODE_TABLE>(), FD_MODE_TABLE>(     \
+        shots, prefix, nshots, ov, grid, s);
+#define FD_PERCELL_OCC(TX, TY)                                                                \
+  case kModePerCell:                                                                          \
+    return occupancy_one<FD_R, TX, TY, pf_of<FD_R, TX, TY, FD_MODE_PERCELL>(), FD_MODE_PERCELL>(); \
+  case kModeTable:                                                                            \
+    return occupancy_one<FD_R, TX, TY, pf_of<FD_R, TX, TY, FD_MODE_TABLE>(), FD_MODE_TABLE>();
 #define FD_PF(TX, TY) pf_of<FD_R, TX, TY, 0>()
 
 template <>
@@ -81,7 +95,7 @@ cudaError_t launch_sweep_r<FD_R>(const TileShape& t, int mode, const ShotDesc* s
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 1>(shots, prefix, nshots, ov, grid, s); \
       case kModeAdjoint:                                                                  \
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(shots, prefix, nshots, ov, grid, s); \
-      FD_PERCELL(launch_one, TX, TY)(shots, prefix, nshots, ov, grid, s);                 \
+      FD_PERCELL_LAUNCH(TX, TY)                                                           \
       default: return cudaErrorInvalidValue;                                              \
     }                                                                                     \
   }
@@ -98,7 +112,7 @@ int sweep_blocks_per_sm_r<FD_R>(const TileShape& t, int mode) {
       case kModeForward: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 0>(); \
       case kModeStoreE: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 1>();  \
       case kModeAdjoint: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(); \
-      FD_PERCELL(occupancy_one, TX, TY)();                                      \
+      FD_PERCELL_OCC(TX, TY)                                                    \
       default: return 0;                                                        \
     }                                                                           \
   }

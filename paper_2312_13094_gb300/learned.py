@@ -10,7 +10,10 @@ Setting (coarse solve = every second fine node, twice the time step):
   coarse  (n/2)^3 + nbl_f/2, h_c = 2 h_f, space order 8 (plain or learned),
           dt_c = 2 dt_f, nt_c = nt_f / 2 steps; coarse rec[k] vs fine rec[2k].
 Velocity models: 3-8 horizontal layers, v in [1.5, 4.5] km/s, interfaces
-smoothed over 40 m, drawn with seeded splitmix64 streams.
+smoothed over 40 m, drawn with seeded splitmix64 streams.  The source and the
+receivers sit on multiples of 4 h_f, which are grid nodes of every spacing
+compared (h_f, 4/3 h_f, 2 h_f), so no configuration is judged on its point
+interpolation.
 """
 from __future__ import annotations
 
@@ -23,17 +26,18 @@ from . import workloads as wl
 
 
 def pair(seed: int, n: int = 512, h: float = 10.0, dt: float = 0.8, nt: int = 1250,
-         nbl: int = 40, f_hz: float = 12.0, nrec: int = 256):
-    """Fine and coarse workloads on the same seeded layered model."""
-    assert n % 2 == 0 and nt % 2 == 0 and nbl % 2 == 0
+         nbl: int = 40, f_hz: float = 12.0, rec_every: int = 4):
+    """Fine and coarse workloads on the same seeded layered model: the source
+    near the centre in x/y at depth 8 h, receivers on a line along x every
+    `rec_every` fine cells (a multiple of 4) through the source's y, at
+    depth 4 h."""
+    assert n % 2 == 0 and nt % 2 == 0 and nbl % 2 == 0 and rec_every % 4 == 0
     nf = (n, n, n)
     v = wl.layered_model(nf, h, seed)
-    ext = (n - 1) * h
-    # source at the centre in x/y, 10 fine cells deep; receivers on a line
-    src = np.array([[n // 2 * h, n // 2 * h, 10 * h]])
-    xs = np.arange(nrec) * 2 * h * max(1, (n // 2 - 1) // max(nrec - 1, 1))
-    xs = xs[xs <= ext]
-    rec = np.stack([xs, np.full(len(xs), n // 2 * h), np.full(len(xs), 4 * h)], 1)
+    c = int(round(n / 2 / 4)) * 4
+    src = np.array([[c * h, c * h, 8 * h]])
+    xs = np.arange(0, n, rec_every) * h
+    rec = np.stack([xs, np.full(len(xs), c * h), np.full(len(xs), 4 * h)], 1)
     wav_f = wl.ricker(nt, dt, f_hz).reshape(nt, 1)
     fine = dict(name=f"fine {n}^3 h{h:g} SO16", n=nf, h=h, space_order=16, nbl=nbl, dt=dt,
                 nt=nt, v=v, src=src, rec=rec, wavelet=wav_f, f0=f_hz)
@@ -45,14 +49,44 @@ def pair(seed: int, n: int = 512, h: float = 10.0, dt: float = 0.8, nt: int = 12
     return fine, coarse
 
 
-def run_forward(w, device=0, net=None, space_order=None, timed=False):
-    """Receivers of one forward run (and its device time in ms if timed)."""
+# Plain configurations between the coarse and the fine grid, (h, space
+# order, dt): dt is a multiple of the fine 0.8 ms so that receiver times
+# coincide, and within each stencil's stability limit at v = 4.5 km/s.
+LADDER = ((20.0, 8, 0.8), (40.0 / 3.0, 8, 0.8), (40.0 / 3.0, 16, 0.8), (10.0, 8, 0.8))
+
+
+def plain_config(seed: int, h: float, space_order: int, dt: float, n: int = 512,
+                 h_f: float = 10.0, dt_f: float = 0.8, nt_f: int = 1250, nbl_m: float = 400.0,
+                 f_hz: float = 12.0):
+    """The fine workload's medium, source and receivers on a plain grid of
+    spacing h (the same physical box, sponge about nbl_m thick); its
+    receivers sample the fine times k * dt."""
+    fine, _ = pair(seed, n=n, h=h_f, dt=dt_f, nt=nt_f, f_hz=f_hz)
+    ext = (n - 1) * h_f
+    ns = int(np.ceil(ext / h - 1e-9)) + 1
+    nd = (ns, ns, ns)
+    v = wl.layered_model(nd, h, seed, depth_m=n * h_f)
+    nt = int(round(nt_f * dt_f / dt))
+    return dict(name=f"plain {ns}^3 h{h:.4g} SO{space_order}", n=nd, h=h,
+                space_order=space_order, nbl=int(round(nbl_m / h)), dt=dt, nt=nt, v=v,
+                src=fine["src"], rec=fine["rec"],
+                wavelet=wl.ricker(nt, dt, f_hz).reshape(nt, 1), f0=f_hz,
+                stride=int(round(dt / dt_f)))
+
+
+def run_forward(w, device=0, net=None, space_order=None, timed=False, table=0):
+    """Receivers of one forward run (and its device time in ms if timed).
+    With a network: per-cell weight fields, or with table > 0 the network
+    tabulated at that many Courant numbers (fd_set_learned_table)."""
     import torch
     so = w["space_order"] if space_order is None else space_order
     ww = dict(w, space_order=so)
     with fd.Grid.from_workload(ww, device=device) as g:
         g.set_model(w["v"])
-        if net is not None:
+        if net is not None and table:
+            fd.check(fd.fd_set_learned_table(g.handle, net, float(w["f0"]), int(table)),
+                     "fd_set_learned_table")
+        elif net is not None:
             fd.check(fd.fd_set_learned_coefficients(g.handle, net, float(w["f0"])),
                      "fd_set_learned_coefficients")
         rec = torch.zeros((w["nt"], len(w["rec"])), device=f"cuda:{device}")
@@ -212,18 +246,29 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True):
+def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True, ladder=False):
     """Per held-out model: receiver rel. L2 of coarse plain and coarse learned
-    against the fine SO 16 solve (fine rec[2k]), and the GPU times."""
+    against the fine SO 16 solve (fine rec[2k]), and the GPU times; with
+    ladder, also the plain configurations of LADDER."""
     rows = []
     for s in seeds:
         fine, coarse = pair(s, n=n, nt=nt)
         rf, tf = run_forward(fine, device, timed=timed)
         ref = rf[::2]
+        extra = {}
+        if ladder:
+            for (hh, so, dt) in LADDER:
+                w = plain_config(s, hh, so, dt, n=n, nt_f=nt)
+                r, t = run_forward(w, device, timed=timed)
+                key = f"h{hh:.4g}_so{so}"
+                extra[key] = rel_l2(r, rf[::w["stride"]][:len(r)])
+                extra["ms_" + key] = t
         rp, tp = run_forward(coarse, device, timed=timed)
         r16, t16 = run_forward(coarse, device, space_order=16, timed=timed)
         rl, tlr = run_forward(coarse, device, net=net.handle, timed=timed)
+        rt, ttb = run_forward(coarse, device, net=net.handle, timed=timed, table=256)
         rows.append(dict(seed=s, plain=rel_l2(rp, ref), plain16=rel_l2(r16, ref),
-                         learned=rel_l2(rl, ref), ms_fine=tf, ms_plain=tp, ms_plain16=t16,
-                         ms_learned=tlr))
+                         learned=rel_l2(rl, ref), learned_table=rel_l2(rt, ref), ms_fine=tf,
+                         ms_plain=tp, ms_plain16=t16, ms_learned=tlr, ms_learned_table=ttb,
+                         **extra))
     return rows

@@ -138,13 +138,15 @@ def acoustic_512(n: int = 512, nt: int = 1000, seed: int = 2, nbl: int = 40):
                 wavelet=ricker(nt, dt, 15.0).reshape(nt, 1), f0=15.0)
 
 
-def layered_model(n, h, seed: int, vmin=1.5, vmax=4.5, width_m=40.0):
+def layered_model(n, h, seed: int, vmin=1.5, vmax=4.5, width_m=40.0, depth_m=None):
     """3-8 horizontal layers, velocities i.i.d. U[vmin, vmax], interface depths
-    uniform in the column, interfaces tanh-smoothed."""
+    uniform in [0, depth_m) (default: the column, n_z h), interfaces
+    tanh-smoothed.  The same seed and depth_m give the same medium sampled at
+    any spacing h."""
     u = uniform(seed, 32)
     nl = 3 + int(u[0] * 6)  # 3..8
     vels = list(vmin + (vmax - vmin) * u[1:1 + nl])
-    depth = n[2] * h
+    depth = n[2] * h if depth_m is None else depth_m
     ifs = sorted(depth * u[10:10 + nl - 1])
     col = smooth_layers(n, h, ifs, vels, width_m)
     v = np.broadcast_to(col[:, None, None].astype(np.float32),

@@ -142,6 +142,52 @@ def test_learned_weights_on_a_grid_match_oracle(fd, learned):
     net.close()
 
 
+@pytest.mark.parametrize("nodes", [2, 64, 256])
+def test_learned_table_on_a_grid_matches_oracle(fd, learned, nodes):
+    """Table mode: the network at `nodes` Courant numbers over the model's
+    range, interpolated per point, against the oracle's per-cell forward with
+    the FP64 table weights of every padded cell."""
+    w = _percell_workload()
+    th = mlp.init_params(9, scale_out=1.0).astype(np.float32)
+    net = learned.Network(th)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        fd.check(fd.fd_set_learned_table(g.handle, net.handle, w["f0"], nodes), "table")
+        rec = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec), "fd_forward")
+    og = oracle.Grid(n=w["n"], h=w["h"], dt=w["dt"], R=4, nbl=w["nbl"])
+    v_pad = 1.0 / np.sqrt(oracle.pad_model(og, 1.0 / w["v"].astype(np.float64) ** 2))
+    v = w["v"].astype(np.float64)
+    lo, hi = v.min() * w["dt"] / w["h"], v.max() * w["dt"] / w["h"]
+    c_pad = mlp.table_coefficients(th.astype(np.float64), v_pad * w["dt"] / w["h"], w["h"],
+                                   w["dt"], w["f0"], nodes, lo, hi, oracle.fd_coefficients(4))
+    _, ref = _oracle_percell(w, c_pad)
+    assert np.linalg.norm(rec - ref) / np.linalg.norm(ref) <= 1e-5
+    net.close()
+
+
+def test_table_mode_is_refused_by_the_adjoint_and_reset_by_plain_weights(fd, learned):
+    w = _percell_workload()
+    net = learned.Network(mlp.init_params(9, scale_out=1.0).astype(np.float32))
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        assert fd.fd_set_learned_table(g.handle, net.handle, w["f0"], 1) == fd.FD_ERR_ARG
+        fd.check(fd.fd_set_learned_table(g.handle, net.handle, w["f0"], 16), "table")
+        grad = np.zeros(g.phys_shape, np.float32)
+        d = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        st, _ = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], d, 4, grad)
+        assert st == fd.FD_ERR_STATE
+        fd.check(fd.fd_set_coefficients(g.handle, None, fd.FD_COEF_TAYLOR), "taylor")
+        plain = np.zeros((w["nt"], len(w["rec"])), np.float32)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], plain), "fd_forward")
+    with fd.Grid.from_workload(w) as g2:
+        g2.set_model(w["v"])
+        ref = np.zeros_like(plain)
+        fd.check(g2.forward(w["src"], w["wavelet"], w["rec"], ref), "fd_forward")
+    np.testing.assert_array_equal(plain, ref)
+    net.close()
+
+
 def test_training_lowers_the_coarse_step_error_on_held_out_models(learned):
     """What the trained network gains over plain SO 8 weights: on fine-run
     samples of models it has not seen (fine 96^3 SO 16 vs coarse 48^3 at
@@ -152,7 +198,7 @@ def test_training_lowers_the_coarse_step_error_on_held_out_models(learned):
     which no per-cell weights can remove, so they are not asserted here (the
     512^3 / 256^3 workload measures them over km of propagation)."""
     import torch
-    kw = dict(n=96, nt=700, nbl=16, f_hz=12.0, nrec=40)
+    kw = dict(n=96, nt=700, nbl=16, f_hz=12.0, rec_every=4)
 
     def data(seeds):
         out = []

@@ -64,3 +64,53 @@ def test_adam_first_step_is_lr_times_sign():
     g = np.linspace(-3, 2, 11) + 0.05
     new, m, v = mlp.adam(th, g, np.zeros(11), np.zeros(11), 1, lr=0.01, eps=0.0)
     np.testing.assert_allclose(new - th, -0.01 * np.sign(g), rtol=1e-12)
+
+
+def _table_case():
+    cT = oracle.fd_coefficients(4)
+    th = mlp.init_params(3, scale_out=1.0)
+    lo, hi, h, dt, f = 0.1, 0.45, 20.0, 1.6, 12.0
+    C = np.random.default_rng(0).uniform(lo, hi, 4000)
+    X = np.stack([C, np.full_like(C, h / 10), np.full_like(C, dt), np.full_like(C, f / 10)], 1)
+    return cT, th, lo, hi, h, dt, f, C, mlp.coefficients(th, X, cT)
+
+
+def test_table_weights_equal_the_network_at_the_nodes():
+    cT, th, lo, hi, h, dt, f, _, _ = _table_case()
+    n = 33
+    Ci = np.sqrt(lo * lo + (hi * hi - lo * lo) * np.arange(n) / (n - 1))
+    X = np.stack([Ci, np.full(n, h / 10), np.full(n, dt), np.full(n, f / 10)], 1)
+    np.testing.assert_allclose(mlp.table_coefficients(th, Ci, h, dt, f, n, lo, hi, cT),
+                               mlp.coefficients(th, X, cT), rtol=1e-13, atol=0)
+
+
+def test_table_of_a_zero_network_is_the_taylor_stencil_everywhere():
+    cT, _, lo, hi, h, dt, f, C, _ = _table_case()
+    th0 = np.zeros(mlp.NPARAM)
+    t = mlp.table_coefficients(th0, C, h, dt, f, 17, lo, hi, cT)
+    np.testing.assert_array_equal(t, np.broadcast_to(cT[1:5], t.shape))
+
+
+def test_table_clamps_outside_the_node_range_and_handles_one_velocity():
+    cT, th, lo, hi, h, dt, f, _, _ = _table_case()
+    t = mlp.table_coefficients(th, np.array([lo - 0.05, lo, hi, hi + 0.05]), h, dt, f, 9,
+                               lo, hi, cT)
+    np.testing.assert_array_equal(t[0], t[1])
+    np.testing.assert_array_equal(t[2], t[3])
+    same = mlp.table_coefficients(th, np.array([0.3, 0.3]), h, dt, f, 5, 0.3, 0.3, cT)
+    X = np.array([[0.3, h / 10, dt, f / 10]])
+    np.testing.assert_allclose(same, np.repeat(mlp.coefficients(th, X, cT), 2, 0), rtol=1e-13)
+
+
+def test_table_weights_converge_to_the_network_at_second_order():
+    """Linear interpolation error falls about 16x for 4x the nodes where the
+    network is smooth (8x here, with the ReLU kinks); a slip in the
+    interpolation weight (f against 1 - f) leaves first-order error (4x)."""
+    cT, th, lo, hi, h, dt, f, C, direct = _table_case()
+
+    def rms(n):
+        t = mlp.table_coefficients(th, C, h, dt, f, n, lo, hi, cT)
+        return np.sqrt(np.mean((t - direct) ** 2)) / np.sqrt(np.mean(direct ** 2))
+
+    assert rms(32) / rms(128) > 6.0
+    assert rms(256) < 1e-6
