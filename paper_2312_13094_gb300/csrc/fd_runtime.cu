@@ -192,10 +192,16 @@ int sweep_ctas(int R, const TileShape& t, int mode) {
   return std::max(1, per) * std::max(1, sms);
 }
 
-int lockstep_ctas(int R, const TileShape& t, int mode, long long columns) {
+int lockstep_chunks(int R, long long slots, long long columns, int Nz) {
+  // at least 8R planes per chunk: each chunk re-reads 2R halo planes
+  const long long kmax = std::max<long long>(1, Nz / (8 * R));
+  return int(std::min<long long>(slots / columns, kmax));
+}
+
+int lockstep_ctas(int R, const TileShape& t, int mode, long long columns, int Nz) {
   const int slots = sweep_ctas(R, t, mode);
   if (t.ctas > 0 || columns <= 0 || columns > slots) return slots;
-  return int(columns * (slots / columns));
+  return int(columns * lockstep_chunks(R, slots, columns, Nz));
 }
 
 const TileShape kShapes[kNumShapes] = {
@@ -206,12 +212,14 @@ const TileShape kShapes[kNumShapes] = {
 // L2.  The k T chunks land on the SMs as evenly as the block scheduler can
 // place them, so the slowest SM holds ceil(k T / SMs) chunks: among the
 // lockstep shapes the one with the fewest points on that SM wins, then the
-// wider tile, then the taller one.  Without a lockstep shape, the shape
-// with the most resident warps (then the widest, then the tallest) runs the
-// equal-share sweep, whose shares are balanced by construction.  Measured on
-// GB300 (Gpts/s): SO 8 592^3 lockstep 64x8 283, 32x16 275, 128x8 256, 32x8
-// 250, 64x16 245; SO 8 768^3 sweep 128x8 255, 64x16 228, 64x8 203, 32x16 183,
-// 32x8 148; SO 16 592^3 sweep 32x16 (12 warps per SM) 156, 128x8 (8) 145.
+// wider tile, then the taller one.  Without a lockstep shape the widest tile
+// (then the tallest) among those with the most resident warps, counting 16
+// or more warps per SM as enough, runs the equal-share sweep, whose shares
+// are balanced by construction.  Measured on GB300 (Gpts/s): SO 8 592^3
+// lockstep 64x8 293, 32x16 285, 32x8 260, 128x8 246 and 64x16 221 (sweeps);
+// SO 8 768^3 sweep 128x8 (16 warps per SM) 260, 64x16 (16) 235, 64x8 (20)
+// 206, 32x16 (20) 178, 32x8 (20) 155; SO 16 592^3 sweep 32x16 (12) 160,
+// 128x8 (8) 145.
 TileShape default_shape(int R, int Nx, int Ny, int Nz) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -227,7 +235,7 @@ TileShape default_shape(int R, int Nx, int Ny, int Nz) {
     const int bx = 4 * t.tx, by = t.ty;
     const long long T = (long long)((Nx + bx - 1) / bx) * ((Ny + by - 1) / by);
     const long long slots = sweep_ctas(R, t, kModeForward);
-    const long long warps = slots * (t.tx * t.ty / 32);
+    const long long warps = std::min<long long>(16, slots / sms * (t.tx * t.ty / 32));
     if (best_sweep < 0 || warps > best_warps ||
         (warps == best_warps && wider(t, kShapes[best_sweep]))) {
       best_sweep = i;
@@ -236,7 +244,7 @@ TileShape default_shape(int R, int Nx, int Ny, int Nz) {
     if (T <= slots) {
       // k chunks of Nz / k planes per column; the busiest SM holds
       // ceil(k T / SMs) chunks
-      const long long k = slots / T;
+      const long long k = lockstep_chunks(R, slots, T, Nz);
       const long long load = (k * T + sms - 1) / sms * (long long)(bx * by) * Nz / k;
       if (best < 0 || load < best_load || (load == best_load && wider(t, kShapes[best]))) {
         best = i;
@@ -520,7 +528,7 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   // fall on chunk boundaries), so every CTA walks z in step with its
   // neighbours, which share halos in L2; otherwise equal contiguous shares
   // of all the (tile, plane) units over every resident slot
-  int G = lockstep_ctas(g->R, g->shape, mode, (long long)g->tiles_x * g->tiles_y);
+  int G = lockstep_ctas(g->R, g->shape, mode, (long long)g->tiles_x * g->tiles_y, g->Nz);
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
   struct {

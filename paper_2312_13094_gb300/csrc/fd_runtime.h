@@ -130,9 +130,11 @@ cudaError_t launch_sweep(int R, const TileShape& t, int mode, const ShotDesc* sh
                          const long long* prefix, int nshots, const StepOverride& ov, int grid,
                          cudaStream_t s);
 int sweep_ctas(int R, const TileShape& t, int mode);
-// CTAs of one step launch: k = slots / columns per column when the columns fit
-// in the resident slots (lockstep z chunks), else every resident slot
-int lockstep_ctas(int R, const TileShape& t, int mode, long long columns);
+// CTAs of one step launch: k z chunks per column when the columns fit in the
+// resident slots (lockstep), else every resident slot; k = slots / columns,
+// capped so that a chunk holds at least 8R of the Nz planes
+int lockstep_chunks(int R, long long slots, long long columns, int Nz);
+int lockstep_ctas(int R, const TileShape& t, int mode, long long columns, int Nz);
 void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d);
 StepArgs base_args(fd_grid g);
 int forward_mode(fd_grid g);  // kModeForward, kModePerCell or kModeTable
