@@ -164,10 +164,13 @@ fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
                            int32_t flags);
 
 /* Chooses the stencil tile (tile_x x tile_y points per CTA column) and the
- * number of persistent CTAs of each step launch (0: as many as are resident
- * on all SMs at once).  Each CTA sweeps an equal contiguous share of the
- * grid's (tile, z plane) units.  Compiled tiles: 64x16, 128x8, 32x16, 64x8,
- * 32x8.
+ * number of persistent CTAs of each step launch.  Each CTA sweeps an equal
+ * contiguous share of the grid's (tile, z plane) units.  ctas = 0 picks the
+ * count: when all tile columns fit in the CTAs resident at once, k equal z
+ * chunks per column (all columns advance together and share halos in L2),
+ * else as many CTAs as are resident on all SMs.  Compiled tiles: 64x16,
+ * 128x8, 32x16, 64x8, 32x8.  fd_create_grid starts from a default chosen by
+ * the load of the busiest SM.
  * Errors: FD_ERR_ARG for a tile that is not compiled or ctas < 0. */
 fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas);
 
