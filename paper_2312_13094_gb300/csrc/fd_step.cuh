@@ -272,8 +272,14 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                   z + j * a.Nz, bar);
   };
 
+  // the u^n ring is refilled by thread 0, the u^{n-1}/A ring by the first
+  // thread of warp 1, so that no single warp carries both after the barrier
+  constexpr int kAuxTid = 32;
+  static_assert(C::NT > kAuxTid, "CTAs have at least two warps");
   if (tid == 0) {
     for (int j = 0; j < C::SU; ++j) issue_u(j, j * C::UPITCH);
+  }
+  if (tid == kAuxTid) {
     for (int i = 0; i < C::SA; ++i) issue_a(i, i * C::TPITCH);
   }
 
@@ -520,10 +526,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         }
 
         if (__syncthreads_or(bad)) goto fail;
-        if (tid == 0) {
-          issue_u(jk + C::SU, sk * C::UPITCH);
-          issue_a(ik + C::SA, sa * C::TPITCH);
-        }
+        if (tid == 0) issue_u(jk + C::SU, sk * C::UPITCH);
+        if (tid == kAuxTid) issue_a(ik + C::SA, sa * C::TPITCH);
         sk = (sk + 1 == C::SU) ? 0 : sk + 1;
         sn = (sn + 1 == C::SU) ? 0 : sn + 1;
         pn ^= (sn == 0) ? 1u : 0u;
@@ -545,13 +549,15 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   return;
 
 fail:
+  // each issuing thread waits (bounded) for the copies it still has in flight
   if (tid == 0) {
     atomicOr(a.err, 1);
-    // wait (bounded) for every copy this CTA still has in flight
     for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
       if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
       mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, ov.spin_limit);
     }
+  }
+  if (tid == kAuxTid) {
     for (int i = max(0, ia_next - C::SA); i < ia_next; ++i)
       mbar_wait(bar_a0 + 8 * (i % C::SA), (i / C::SA) & 1, ov.spin_limit);
   }
