@@ -43,6 +43,12 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _out_dir():
+    """Where side outputs go (autotune cache, trained parameters):
+    $FD_BENCH_OUT, else bench_out/ beside this file."""
+    return os.environ.get("FD_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     for name in ("fd_step.cuh", "fd_step_inst.cuh", "fd_internal.h"):
@@ -383,7 +389,8 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     pts = sum(int(np.prod(_padded(w))) for w in shots)
     nt = shots[0]["nt"]
-    os.environ.setdefault("FD_AUTOTUNE_CACHE", os.path.join(ROOT, "gpurun_out", "autotune.txt"))
+    os.makedirs(_out_dir(), exist_ok=True)
+    os.environ.setdefault("FD_AUTOTUNE_CACHE", os.path.join(_out_dir(), "autotune.txt"))
     with torch.cuda.stream(stream):
         grids, spec = [], []
         for w in shots:
@@ -448,8 +455,8 @@ def run_learned(args):
     t_train = time.time() - t1
     rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt,
                        ladder=args.ladder)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    np.save(os.path.join(ROOT, "gpurun_out", "learned_params.npy"), net.params())
+    os.makedirs(_out_dir(), exist_ok=True)
+    np.save(os.path.join(_out_dir(), "learned_params.npy"), net.params())
 
     def mean(key):
         return float(np.mean([r[key] for r in rows]))

@@ -12,7 +12,7 @@ Setting (coarse solve = every second fine node, twice the time step):
 Velocity models: 3-8 horizontal layers, v in [1.5, 4.5] km/s, interfaces
 smoothed over 40 m, drawn with seeded splitmix64 streams.  The source and the
 receivers sit on multiples of 4 h_f, which are grid nodes of every spacing
-compared (h_f, 4/3 h_f, 2 h_f), so no configuration is judged on its point
+compared (h_f, 4/3 h_f, 2 h_f), so no configuration is scored on its point
 interpolation.
 """
 from __future__ import annotations
