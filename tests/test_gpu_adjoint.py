@@ -138,6 +138,6 @@ def test_autograd_function_gives_the_oracle_gradient(fd):
         loss.backward()
     ref, rloss, _ = oracle.adjoint_gradient(og_of(w), m64, w["nt"], w["src"], w["wavelet"],
                                             w["rec"], d_obs=d_obs.astype(np.float64))
-    assert abs(float(loss) - rloss) <= 1e-5 * abs(rloss)
+    assert abs(float(loss.detach()) - rloss) <= 1e-5 * abs(rloss)
     grad = m.grad.cpu().numpy()
     assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) <= 1e-4

@@ -240,3 +240,67 @@ def test_degenerate_one_cell_grid_without_layer(fd):
     rec, u = run_gpu(fd, w)
     rrec, ru = run_oracle(w)
     assert rel(rec, rrec) <= TOL and rel(u, ru) <= TOL
+
+
+def test_grid_beyond_2_32_cells_sampled(fd):
+    """1600^3 + 40-cell layer (1680^3 = 4.74e9 cells per field, past 2^32): one
+    step from a random state generated on the device, checked at interior
+    points whose flat index exceeds 2^32 and at random interior points.  An
+    interior point's step depends only on its (2R+1)^3 neighbourhood and its
+    own m (b = 0 there), so each is compared with the oracle on a 9^3 window
+    grid with no layer around it."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150e9:
+        pytest.skip("needs about 130 GB of free device memory")
+    n, nbl, R, h = 1600, 40, 4, 10.0
+    N = n + 2 * nbl
+    assert N ** 3 > 2 ** 32
+    dev = "cuda"
+    zz = torch.arange(n, device=dev, dtype=torch.float32)
+    v = (2.0 + 0.1 * torch.sin(0.017 * zz)[:, None, None]
+         + 0.2 * torch.cos(0.013 * zz)[None, :, None]
+         + 0.3 * torch.sin(0.011 * zz)[None, None, :]).contiguous()
+    dt = 0.4 * h / 2.6
+    w = dict(name="max", n=(n, n, n), h=h, space_order=2 * R, nbl=nbl, dt=dt, nt=1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(21)
+    up = torch.rand((N, N, N), generator=gen, device=dev) - 0.5
+    uc = torch.rand((N, N, N), generator=gen, device=dev) - 0.5
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(v)
+        g.set_wavefield(up, uc)
+        fd.check(g.propagate(0, 1), "fd_propagate")
+        out = torch.empty((N, N, N), device=dev)
+        g.get_wavefield(None, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    zlo = (2 ** 32) // (N * N) + 1
+    pts = np.concatenate([
+        np.stack([rng.integers(zlo, nbl + n, 300), rng.integers(nbl, nbl + n, 300),
+                  rng.integers(nbl, nbl + n, 300)], 1),
+        np.stack([rng.integers(nbl, nbl + n, 200) for _ in range(3)], 1),
+        np.array([[nbl + n - 1, nbl + n - 1, nbl + n - 1], [nbl, nbl, nbl],
+                  [nbl + n - 1, nbl, nbl + n - 1]])])
+    assert ((pts[:, 0].astype(np.int64) * N + pts[:, 1]) * N + pts[:, 2] > 2 ** 32).sum() >= 300
+    off = np.arange(-R, R + 1)
+    oz, oy, ox = np.meshgrid(off, off, off, indexing="ij")
+    win = (((pts[:, 0, None] + oz.ravel()) * N + pts[:, 1, None] + oy.ravel()) * N
+           + pts[:, 2, None] + ox.ravel())
+    win_t = torch.from_numpy(win.astype(np.int64)).to(dev)
+    up_w = up.view(-1)[win_t].cpu().numpy().astype(np.float64)
+    uc_w = uc.view(-1)[win_t].cpu().numpy().astype(np.float64)
+    ctr = torch.from_numpy(((pts[:, 0].astype(np.int64) * N + pts[:, 1]) * N + pts[:, 2])).to(dev)
+    got = out.view(-1)[ctr].cpu().numpy()
+    vp = v[torch.from_numpy(pts[:, 0] - nbl).to(dev), torch.from_numpy(pts[:, 1] - nbl).to(dev),
+           torch.from_numpy(pts[:, 2] - nbl).to(dev)].cpu().numpy().astype(np.float64)
+    del up, uc, out, v
+    torch.cuda.empty_cache()
+    og = oracle.Grid(n=(2 * R + 1,) * 3, h=h, dt=dt, R=R, nbl=0)
+    c = (2 * R + 1) ** 3 // 2
+    ref = np.empty(len(pts))
+    for i in range(len(pts)):
+        m = np.full((2 * R + 1,) * 3, 1.0 / vp[i] ** 2)
+        ref[i] = oracle.step_points(og, m, vp[i], up_w[i].reshape((2 * R + 1,) * 3),
+                                    uc_w[i].reshape((2 * R + 1,) * 3), np.array([c]))[0]
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
