@@ -440,19 +440,25 @@ def run_learned(args):
     import torch
     from paper_2312_13094_gb300 import learned as lr
     n, nt = args.n, (args.nt if args.nt != 1000 else 1250)
-    t0 = time.time()
-    data = []
-    for s in range(args.train_models):
-        fine, coarse = lr.pair(s, n=n, nt=nt)
-        data.append(lr.training_samples(fine, coarse, ncell=16384, ntimes=8, seed=s))
-    S = torch.cat(data)
-    S = S[torch.randperm(S.shape[0], generator=torch.Generator().manual_seed(0)).to(S.device)]
-    t_data = time.time() - t0
-    net = lr.Network(lr.init_params(0, scale_out=0.0))
-    l0 = net.loss_grad(S)[0]
-    t1 = time.time()
-    l1 = net.train(S, epochs=args.epochs, batch=65536, lr=1e-3)
-    t_train = time.time() - t1
+    if args.params:
+        # evaluate a network trained earlier (FD_MLP_NPARAM floats, .npy)
+        net = lr.Network(np.load(args.params).astype(np.float32))
+        S = torch.zeros((0, 10))
+        l0 = l1 = t_data = t_train = None
+    else:
+        t0 = time.time()
+        data = []
+        for s in range(args.train_models):
+            fine, coarse = lr.pair(s, n=n, nt=nt)
+            data.append(lr.training_samples(fine, coarse, ncell=16384, ntimes=8, seed=s))
+        S = torch.cat(data)
+        S = S[torch.randperm(S.shape[0], generator=torch.Generator().manual_seed(0)).to(S.device)]
+        t_data = time.time() - t0
+        net = lr.Network(lr.init_params(0, scale_out=0.0))
+        l0 = net.loss_grad(S)[0]
+        t1 = time.time()
+        l1 = net.train(S, epochs=args.epochs, batch=65536, lr=1e-3)
+        t_train = time.time() - t1
     rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt,
                        ladder=args.ladder)
     os.makedirs(_out_dir(), exist_ok=True)
@@ -493,6 +499,8 @@ def main():
     ap.add_argument("--train-models", type=int, default=200)
     ap.add_argument("--test-models", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--params", default="",
+                    help="learned workload: evaluate these network parameters (.npy), no training")
     ap.add_argument("--ladder", action="store_true",
                     help="learned workload: also time plain SO 8/16 at h 16 and 12.8 m")
     ap.add_argument("--gpus", type=int, default=1)
