@@ -81,6 +81,8 @@ def _load():
                                             ctypes.c_int32, _D, _D, _D, _D,
                                             _D, _D]
         lib.or_adjoint_gradient.restype = ctypes.c_int32
+        lib.or_step_slab.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_int64, _D]
+        lib.or_step_slab.restype = ctypes.c_int32
         lib.or_step_points.argtypes = [G, _D, ctypes.c_double, _D, _D, _D,
                                        ctypes.c_int64, _I64, _D]
         _lib = lib
@@ -192,6 +194,23 @@ def step(g: Grid, m_pad, b, u_prev, u_cur, *, coef=None, percell=None,
                     _p(_f64(percell)), _p(_f64(u_prev)), _p(_f64(u_cur)), ns,
                     si.ctypes.data_as(_I64), _p(sv), _p(L), _p(out), _p(e))
     return out, e
+
+
+def step_slab(g: Grid, m_pad_s, b_s, u_prev_s, u_cur_x, coef=None):
+    """One source-free step of the owned z planes of a slab (domain
+    decomposition along z): ``u_cur_x`` holds the owned planes with R ghost
+    planes before and after; the other arrays cover the owned planes."""
+    coef = fd_coefficients(g.R) if coef is None else _f64(coef)
+    u_prev_s = _f64(u_prev_s)
+    nzs = u_prev_s.shape[0]
+    assert u_cur_x.shape[0] == nzs + 2 * g.R
+    out = np.zeros(u_prev_s.shape)
+    gc = g.c()
+    r = _load().or_step_slab(ctypes.byref(gc), _p(_f64(m_pad_s)), _p(_f64(b_s)), _p(coef),
+                             _p(u_prev_s), _p(_f64(u_cur_x)), nzs, _p(out))
+    if r != 0:
+        raise ValueError("slab steps need a 3-D, non-periodic grid")
+    return out
 
 
 def step_points(g: Grid, m_phys, vmax: float, u_prev, u_cur, idx, coef=None):

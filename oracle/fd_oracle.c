@@ -233,6 +233,61 @@ void or_step(const or_grid* g, const double* m_pad, const double* b,
   }
 }
 
+/*
+ * The same damped leapfrog step on a z slab of the padded grid, as one rank of
+ * a domain decomposition along z computes it (the paper's basic mode, Sec. III
+ * "halo exchange": each subdomain reads R ghost planes of u^n from its
+ * neighbours before the step).  Owned planes are nzs consecutive padded z
+ * planes; u_cur_x holds them with R ghost planes before and after
+ * ([nzs + 2R][N1][N0], zero where the ghost lies beyond the global grid);
+ * m_pad_s, b_s, u_prev_s and u_next_s cover the owned planes only.  Sources
+ * are not handled here.  Every point is summed in the order of or_laplacian
+ * and updated as in or_step, so a decomposed run reproduces the undecomposed
+ * one bit for bit.  Returns 0, or -1 for a grid that is not 3-D and
+ * non-periodic.
+ */
+int32_t or_step_slab(const or_grid* g, const double* m_pad_s, const double* b_s,
+                     const double* coef, const double* u_prev_s, const double* u_cur_x,
+                     int64_t nzs, double* u_next_s) {
+  if (g->dims != 3 || g->periodic) return -1;
+  int64_t N[3];
+  padded_dims(g, N);
+  const int R = g->R;
+  const double ih2 = 1.0 / (g->h * g->h);
+  const double dt2 = g->dt * g->dt;
+  const int64_t plane = N[0] * N[1];
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int64_t kk = 0; kk < nzs; ++kk)
+    for (int64_t j = 0; j < N[1]; ++j)
+      for (int64_t i = 0; i < N[0]; ++i) {
+        const int64_t o = i + N[0] * j;
+        const double* uc = u_cur_x + (kk + R) * plane;  /* centre plane */
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          acc += coef[0] * uc[o];
+          for (int r = 1; r <= R; ++r) {
+            double up_v, dn_v;
+            if (a == 0) {
+              up_v = i + r < N[0] ? uc[o + r] : 0.0;
+              dn_v = i - r >= 0 ? uc[o - r] : 0.0;
+            } else if (a == 1) {
+              up_v = j + r < N[1] ? uc[o + r * N[0]] : 0.0;
+              dn_v = j - r >= 0 ? uc[o - r * N[0]] : 0.0;
+            } else {
+              up_v = uc[o + r * plane];
+              dn_v = uc[o - r * plane];
+            }
+            acc += coef[r] * (up_v + dn_v);
+          }
+        }
+        const double L = acc * ih2;
+        const int64_t idx = o + kk * plane;
+        const double e = dt2 / m_pad_s[idx] * L;
+        u_next_s[idx] = (2.0 * uc[o] - (1.0 - b_s[idx]) * u_prev_s[idx] + e) / (1.0 + b_s[idx]);
+      }
+  return 0;
+}
+
 /* Forward-Euler heat step u_next = u + dt * L u (Sec. II, Listing 1). */
 void or_heat_step(const or_grid* g, const double* u, double* scratch_L,
                   double* u_next) {

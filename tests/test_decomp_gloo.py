@@ -1,0 +1,91 @@
+"""Domain decomposition along z over CPU ranks (gloo): each rank steps its own
+slab of the padded grid with the FP64 reference step after an R-plane halo
+exchange; the gathered result equals the undecomposed run bit for bit."""
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_13094_gb300 import decomp
+
+
+@pytest.mark.parametrize("Nz,world", [(15, 1), (15, 2), (15, 3), (16, 5), (100, 7)])
+def test_slab_ranges_partition_the_planes(Nz, world):
+    seen, sizes = [], []
+    for r in range(world):
+        z0, n = decomp.slab_range(Nz, world, r)
+        seen.extend(range(z0, z0 + n))
+        sizes.append(n)
+    assert seen == list(range(Nz))
+    assert max(sizes) - min(sizes) <= 1
+
+
+def test_slab_range_rejects_more_ranks_than_planes():
+    with pytest.raises(ValueError):
+        decomp.slab_range(3, 4, 0)
+
+
+def _problem(R):
+    from paper_2312_13094_gb300 import workloads as wl
+    n = (12, 10, 9)
+    h = 10.0
+    v = wl.layered_model(n, h, 3, vmin=1.8, vmax=2.4)
+    g = oracle.Grid(n=n, h=h, dt=0.3 * h / 2.4, R=R, nbl=3)
+    shp = g.padded_shape
+    m_pad = oracle.pad_model(g, 1.0 / v.astype(np.float64) ** 2)
+    b = oracle.damping(g, float(v.max()))
+    return g, m_pad, b, wl.random_state(shp, 1), wl.random_state(shp, 2)
+
+
+@pytest.mark.parametrize("R", [2, 4])
+def test_slab_step_over_the_whole_grid_is_the_full_step(R):
+    g, m_pad, b, up, uc = _problem(R)
+    zero = np.zeros((R,) + up.shape[1:])
+    out = oracle.step_slab(g, m_pad, b, up, np.concatenate([zero, uc, zero]))
+    ref, _ = oracle.step(g, m_pad, b, up, uc)
+    np.testing.assert_array_equal(out, ref)
+
+
+def _rank_main(rank, world, port, R, nt):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}",
+                            world_size=world, rank=rank)
+    try:
+        g, m_pad, b, up, uc = _problem(R)
+        z0, nzs = decomp.slab_range(g.padded_shape[0], world, rank)
+        own = slice(z0, z0 + nzs)
+        prev = up[own].copy()
+        ux = torch.zeros((nzs + 2 * R,) + up.shape[1:], dtype=torch.float64)
+        ux[R:R + nzs] = torch.from_numpy(uc[own])
+        for _ in range(nt):
+            decomp.exchange_halos(ux, R, dist, rank, world)
+            nxt = oracle.step_slab(g, m_pad[own], b[own], prev, ux.numpy())
+            prev = ux[R:R + nzs].numpy().copy()
+            ux[R:R + nzs] = torch.from_numpy(nxt)
+        parts = [None] * world
+        dist.all_gather_object(parts, (z0, ux[R:R + nzs].numpy().copy()))
+        if rank == 0:
+            got = np.concatenate([p for _, p in sorted(parts, key=lambda t: t[0])])
+            pu, cu = up, uc
+            for _ in range(nt):
+                nu, _ = oracle.step(g, m_pad, b, pu, cu)
+                pu, cu = cu, nu
+            np.testing.assert_array_equal(got, cu)
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("world,R", [(2, 2), (3, 4)])
+def test_decomposed_run_over_gloo_ranks_equals_the_undecomposed_run(world, R):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    oracle.build()
+    mp.spawn(_rank_main, args=(world, _free_port(), R, 6), nprocs=world, join=True)
