@@ -433,6 +433,121 @@ def run_batched(args):
           flush=True)
 
 
+def run_decomposed(args):
+    """The headline grid cut into z slabs (fd_set_decomposition) in both
+    exchange modes, against the same grid undecomposed: Gpts/s of whole
+    fd_forward runs (device time, CUDA events), so the difference is what the
+    ghost planes, the halo copies and the extra launches cost on one GPU."""
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    from paper_2312_13094_gb300 import workloads as wl
+    w = wl.acoustic_512(n=args.n, nt=args.nt)
+    npts = int(np.prod(_padded(w)))
+    nt = w["nt"]
+    stream = torch.cuda.Stream()
+    rows = []
+    peak, kind = _peaks()
+    with torch.cuda.stream(stream):
+        g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
+        v_dev = torch.from_numpy(w["v"]).cuda()
+        wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+        rec = torch.zeros((nt, len(w["rec"])), device="cuda")
+        ref = None
+        for nsub, mode in [(1, 0)] + [(p, m) for p in args.slabs for m in (0, 1)]:
+            g.set_decomposition(nsub, mode)
+            g.set_model(v_dev)
+
+            def one():
+                fd.check(g.forward(w["src"], wav, w["rec"], rec), "fd_forward")
+
+            for _ in range(args.warmup):
+                one()
+            launches0 = fd.fd_launch_count()
+            ms = _device_ms(one, stream, args.steps)
+            launches = (fd.fd_launch_count() - launches0) // args.steps
+            if ref is None:
+                ref = rec.clone()
+                same = True
+            else:
+                same = bool(torch.equal(rec, ref))
+            gpts = npts * nt / (ms * 1e-3) / 1e9
+            rows.append({"slabs": nsub, "mode": ["basic", "overlap"][mode], "ms": ms,
+                         "gpts": gpts, "frac": 16 * gpts / peak,
+                         "launches_per_run": int(launches), "receivers_bitwise_equal": same})
+        g.set_decomposition(1)
+        g.close()
+    base = rows[0]["gpts"]
+    for r in rows:
+        r["vs_undecomposed"] = r["gpts"] / base
+    print(json.dumps({"metric": "Gpts/s", "unit": "Gpts/s", "higher_is_better": True,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+                      "data": "synthetic", "peak": peak, "peak_kind": kind,
+                      "config": {"workload": w["name"] + " in z slabs",
+                                 "grid_padded": _padded(w), "nt": nt},
+                      "rows": rows}), flush=True)
+
+
+def run_fwi(args):
+    """A few shot-parallel FWI iterations on the adjoint workload's grid
+    (256^3 + 20-cell layer, SO 8, 500 steps, 25 checkpoints): 4 shots through
+    the Gaussian anomaly, observed data from the true model, start model
+    v = 2.0.  Reports the device time per accepted iteration (every gradient
+    evaluation of all shots, the reduction and the device update), the misfit
+    history and the model error relative to the start."""
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    from paper_2312_13094_gb300 import fwi
+    from paper_2312_13094_gb300 import workloads as wl
+    n = args.n if args.n != 512 else 256
+    nt = args.nt if args.nt != 1000 else 500
+    w = wl.adjoint_256(n=n, nt=nt)
+    w0 = wl.adjoint_256(n=n, nt=nt, anomaly=False)
+    h = w["h"]
+    srcs = [np.array([[x * n * h, y * n * h, n / 4 * h]])
+            for x, y in ((0.3, 0.3), (0.7, 0.3), (0.3, 0.7), (0.7, 0.7))]
+    stream = torch.cuda.Stream()
+    npts = int(np.prod(_padded(w)))
+    with torch.cuda.stream(stream):
+        g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
+        wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+        m_true = torch.from_numpy(1.0 / w["v"].astype(np.float32) ** 2).cuda()
+        d_obs = []
+        for sx in srcs:
+            g.set_model(m_true, fd.FD_MODEL_M)
+            d = torch.zeros((nt, len(w["rec"])), device="cuda")
+            fd.check(g.forward(sx, wav, w["rec"], d), "observed data")
+            d_obs.append(d)
+        shots = fwi.AdjointShots(g, srcs, wav, w["rec"], d_obs, n_checkpoints=25)
+        m0 = torch.from_numpy(1.0 / w0["v"].astype(np.float32) ** 2).cuda()
+        upd = fwi.device_update(1.0 / 3.0 ** 2, 1.0 / 1.5 ** 2)
+        fwi.fwi_loop(m0, len(srcs), shots, upd, iterations=1, step=0.01)  # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m, hist = fwi.fwi_loop(m0, len(srcs), shots, upd, iterations=args.steps, step=0.01)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        g.close()
+    err0 = float((m0 - m_true).double().norm())
+    err = float((m - m_true).double().norm())
+    accepted = len(hist["step"])
+    evals = hist["evals"]
+    peak, kind = _peaks()
+    gbs = 64 * npts * nt * len(srcs) * evals / (ms * 1e-3) / 1e9
+    print(json.dumps({"metric": "s per FWI iteration", "value": ms / 1e3 / max(1, accepted),
+                      "unit": "s", "higher_is_better": False, "iterations": accepted,
+                      "gradient_evaluations": evals, "shots": len(srcs), "dtype": "f32",
+                      "data": "synthetic", "misfit": hist["loss"], "steps": hist["step"],
+                      "model_error_vs_start": err / err0,
+                      "config": {"workload": w["name"] + ", 4 shots, FWI",
+                                 "grid_padded": _padded(w), "checkpoints": 25},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
+                                   "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
+                                   "algorithmic_bytes_per_point_step": 64}}), flush=True)
+
+
 def run_learned(args):
     """Learned per-cell SO 8 weights on the coarse grid vs the plain SO 16
     fine solve: train on fine-run samples of `--train-models` models, then
@@ -495,7 +610,9 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "adjoint", "batched", "learned"])
+                    choices=["headline", "adjoint", "batched", "learned", "decomposed", "fwi"])
+    ap.add_argument("--slabs", type=lambda t: [int(x) for x in t.split(",")], default=[2, 4, 8],
+                    help="decomposed workload: slab counts to time")
     ap.add_argument("--train-models", type=int, default=200)
     ap.add_argument("--test-models", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=20)
@@ -519,8 +636,8 @@ def main():
     if args.workload != "headline":
         import torch
         torch.cuda.set_device(local)
-        {"adjoint": run_adjoint, "batched": run_batched, "learned": run_learned}[
-            args.workload](args)
+        {"adjoint": run_adjoint, "batched": run_batched, "learned": run_learned,
+         "decomposed": run_decomposed, "fwi": run_fwi}[args.workload](args)
         return
     from paper_2312_13094_gb300 import workloads as wl
     w = wl.acoustic_512(n=args.n, nt=args.nt)

@@ -146,9 +146,10 @@ fd_status fd_backward(fd_grid grid, const fd_points* src, const float* wavelet,
                       const fd_points* rec, const float* grad_rec,
                       int32_t n_checkpoints, float* grad_m);
 
-/* Many independent shots (each its own grid, all with the same space order
- * and nt) advanced together: each time step is one persistent launch over a
- * shared {shot, tile} work list; the nt launches are captured in a CUDA
+/* Many independent shots (each its own grid, all with the same space order,
+ * nt and layer width nbl) advanced together: each time step is one
+ * persistent launch over a shared {shot, tile} work list; the nt launches
+ * are captured in a CUDA
  * graph when flags has FD_BATCH_GRAPH.  FD_BATCH_AUTOTUNE times the tile
  * candidates once per (space order, window sizes) and caches the choice.
  * All grids must be on the same device; the first grid's stream is used. */
@@ -162,6 +163,53 @@ typedef struct {
 } fd_shot;
 fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
                            int32_t flags);
+
+/* Domain decomposition along z (Sec. III: the grid is split into
+ * subdomains that each exchange an R-deep halo with their neighbours, in a
+ * "basic" mode that exchanges before every step and a "full" mode that
+ * overlaps the exchange with the CORE points, whose stencils need no halo,
+ * and computes the REMAINDER afterwards).  With nsub > 1 the padded grid's
+ * nz + 2 nbl planes are cut into nsub contiguous slabs of balanced size
+ * (sizes differ by at most one plane); each slab keeps its own two
+ * wavefields and model term with R ghost planes on either side, and every
+ * later fd_forward / fd_propagate on this grid steps the slabs:
+ *   FD_DMP_BASIC    per step, one launch per slab, then device copies that
+ *                   refill every inner ghost plane with the neighbour's
+ *                   edge planes (one copy per face and direction: a z face
+ *                   is contiguous, so nothing is packed);
+ *   FD_DMP_OVERLAP  per step, first the R planes beside each inner face of
+ *                   every slab, then their copies to the neighbours on a
+ *                   second stream while the remaining (core) planes are
+ *                   computed; the next step waits for the copies.
+ * Every point is computed exactly as in the undecomposed run, so receivers
+ * and wavefields are the same bit for bit; the whole-grid state is scattered
+ * into the slabs before a run and gathered back after it, so fd_get_wavefield
+ * and u_out see the usual layout.  All slabs live on the grid's device.
+ * The slabs add 3 (nz + 2 nbl + 2 R nsub) planes of device memory, allocated
+ * here.  nsub = 1 removes the decomposition.  fd_adjoint_gradient,
+ * fd_backward and fd_batch_forward ignore it and step the whole grid; the
+ * FD_DEBUG_SKIP_PLANE hook does not reach slab runs.
+ * Errors: FD_ERR_ARG (bad mode; a slab would hold fewer than R planes, 2R in
+ * overlap mode), FD_ERR_OOM, FD_ERR_CUDA; a run with per-cell weight fields
+ * returns FD_ERR_STATE. */
+enum { FD_DMP_BASIC = 0, FD_DMP_OVERLAP = 1 };
+fd_status fd_set_decomposition(fd_grid grid, int32_t nsub, int32_t mode);
+
+/* One model update of a full-waveform-inversion loop (the paper names FWI
+ * as a user of the propagator, Sec. I and IV-B, without an update rule):
+ * normalised steepest descent on n values,
+ *     alpha = step * max|m| / max|grad|,
+ *     m[i] <- min(max(m[i] - alpha grad[i], m_min), m_max),
+ * so the largest change is `step` times the model's scale.  m (updated in
+ * place) and grad are DEVICE arrays on the current device; the work runs on
+ * `stream` (NULL: the legacy default stream) and has completed on return.
+ * *alpha_out (optional) receives alpha; a zero gradient (or step 0) leaves m
+ * unchanged with alpha 0.  Errors: FD_ERR_ARG (n < 0, null or host arrays,
+ * step < 0, m_min > m_max), FD_ERR_NONFINITE (NaN or Inf in grad; m is then
+ * unchanged), FD_ERR_OOM, FD_ERR_CUDA. */
+fd_status fd_descent_step(int64_t n, float* m, const float* grad, double step,
+                          double m_min, double m_max, void* stream,
+                          double* alpha_out);
 
 /* Chooses the stencil tile (tile_x x tile_y points per CTA column) and the
  * number of persistent CTAs of each step launch.  Each CTA sweeps an equal

@@ -36,6 +36,7 @@ FD_BATCH_GRAPH, FD_BATCH_AUTOTUNE = 1, 2
 FD_DEBUG_SKIP_PLANE, FD_DEBUG_SPIN_LIMIT, FD_DEBUG_NO_GRAPH = 1, 2, 3
 FD_COEF_TAYLOR, FD_COEF_UNIFORM, FD_COEF_PER_CELL = 0, 1, 2
 FD_MLP_NPARAM, FD_MLP_SAMPLE = 5000, 10
+FD_DMP_BASIC, FD_DMP_OVERLAP = 0, 1
 
 
 class fd_grid_desc(ctypes.Structure):
@@ -99,6 +100,9 @@ _SIGS = {
     "fd_forward_noalloc": (_S, [ctypes.POINTER(fd_grid_desc), _P, ctypes.c_int32, _PTS, _P,
                                 _PTS, _P]),
     "fd_set_tile": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "fd_set_decomposition": (_S, [_G, ctypes.c_int32, ctypes.c_int32]),
+    "fd_descent_step": (_S, [ctypes.c_int64, _P, _P, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "fd_set_debug": (_S, [_G, ctypes.c_int32, ctypes.c_int64]),
     "fd_get_info": (_S, [_G, ctypes.POINTER(fd_grid_info)]),
     "fd_set_profiling": (_S, [_G, ctypes.c_int32]),
@@ -220,6 +224,9 @@ class Grid:
     def set_tile(self, tile_x, tile_y, ctas=0):
         check(fd_set_tile(self.handle, tile_x, tile_y, ctas), "fd_set_tile")
 
+    def set_decomposition(self, nsub, mode=FD_DMP_BASIC):
+        check(fd_set_decomposition(self.handle, nsub, mode), "fd_set_decomposition")
+
     def set_debug(self, key, value):
         check(fd_set_debug(self.handle, key, value), "fd_set_debug")
 
@@ -256,6 +263,17 @@ class Grid:
         s, r = Points(src), Points(rec)
         return fd_backward(self.handle, s.ref(), _ptr(wavelet), r.ref(), _ptr(grad_rec),
                            n_checkpoints, _ptr(grad_out))
+
+
+def descent_step(m, grad, step, m_min, m_max, stream=None):
+    """fd_descent_step on two device tensors of equal size (m in place);
+    returns alpha."""
+    if m.numel() != grad.numel():
+        raise ValueError("m and grad differ in size")
+    alpha = ctypes.c_double(0.0)
+    check(fd_descent_step(m.numel(), _ptr(m), _ptr(grad), float(step), float(m_min),
+                          float(m_max), stream, ctypes.byref(alpha)), "fd_descent_step")
+    return alpha.value
 
 
 def batch_forward(shots, flags=FD_BATCH_GRAPH):

@@ -78,6 +78,7 @@ struct Prepared {
   int nshots = 0;
   int ctas = 0;
   float c[kMaxR + 1] = {};  // stencil weights (the same for every shot)
+  int nbl = 0;              // layer width (the same for every shot)
   long long spin_limit = 0;
 };
 
@@ -134,6 +135,7 @@ fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared
   fd_grid g0 = shots[0].grid;
   for (int j = 0; j <= kMaxR; ++j) P.c[j] = j <= R ? float(g0->c[j]) : 0.0f;
   P.spin_limit = g0->spin_limit;
+  P.nbl = g0->d.nbl;
   return FD_OK;
 }
 
@@ -168,6 +170,8 @@ fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileSh
     StepOverride ov;
     memset(&ov, 0, sizeof(ov));
     ov.cur = step & 1;
+    ov.zfirst = 0;
+    ov.nblz = P.nbl;
     ov.inj_row = step;
     ov.rec_row = step;
     ov.spin_limit = P.spin_limit;
@@ -230,8 +234,9 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
       return fail(FD_ERR_STATE, "shot %d uses per-cell weights", i);
     for (int j = 0; j <= g->R && j <= g0->R; ++j)
       if (g->c[j] != g0->c[j]) return fail(FD_ERR_ARG, "shots must share stencil weights");
-    if (g->d.device != g0->d.device || g->R != g0->R || g->d.nt != g0->d.nt)
-      return fail(FD_ERR_ARG, "shots must share device, space order and nt");
+    if (g->d.device != g0->d.device || g->R != g0->R || g->d.nt != g0->d.nt ||
+        g->d.nbl != g0->d.nbl)
+      return fail(FD_ERR_ARG, "shots must share device, space order, nt and layer width");
     for (int j = 0; j < i; ++j)
       if (shots[j].grid == g) return fail(FD_ERR_ARG, "grid used by two shots");
     const int nsrc = shots[i].src ? shots[i].src->n : 0;

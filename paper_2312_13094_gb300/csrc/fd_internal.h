@@ -39,7 +39,7 @@ enum StepMode : int {
 
 // Everything one launch of the step kernel needs besides the tensor maps.
 struct StepArgs {
-  int32_t Nx, Ny, Nz;      // padded extents
+  int32_t Nx, Ny, Nz;      // padded extents (Nz: updated planes per tile column)
   int32_t pitch;           // floats per row of every device array
   int32_t nbl, nx, ny, nz; // layer width and physical extents
   int32_t tiles_x, tiles_y;
@@ -83,6 +83,10 @@ struct ShotDesc {
 // Per-launch values of a sweep: buffer parity, table rows, imaging fields.
 struct StepOverride {
   int cur;            // u[cur] holds u^n
+  int zfirst;         // array plane of the first updated plane of every grid of the
+                      // launch (0 for whole grids; a slab part: its first plane)
+  int nblz;           // layer width in the launch's array planes along z: nbl minus the
+                      // padded z of array plane 0 (nbl for whole grids)
   int inj_row;
   int rec_row;
   int debug_skip_plane;      // test hook: never issue this plane's load (-1)

@@ -584,6 +584,8 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       StepOverride ov;
       memset(&ov, 0, sizeof(ov));
       ov.cur = (cur0 + t) & 1;
+      ov.zfirst = 0;
+      ov.nblz = g->d.nbl;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
       for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
@@ -782,6 +784,7 @@ fd_status fd_destroy_grid(fd_grid g) {
   if (!g) return FD_OK;
   cudaSetDevice(g->d.device);
   if (g->stream) cudaStreamSynchronize(g->stream);
+  decomp_destroy(g);
   if (g->graph_valid) cudaGraphExecDestroy(g->gexec);
   for (int b = 0; b < 2; ++b) {
     if (g->F.u[b]) cudaFree(g->F.u[b]);
@@ -857,6 +860,7 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
   const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;
   if ((nsrc && (!src->xyz || !wavelet)) || (nrec && (!rec->xyz || !rec_out)))
     return fail(FD_ERR_ARG, "points given without their data array");
+  if (g->dmp) return decomp_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
   fd_status st = upload_tables(g, src, 1.0 / g->d.h, rec, g->tab);
   if (st) return st;
   const float* dval = nullptr;

@@ -66,6 +66,8 @@ struct GraphKey {
   float c[kMaxR + 1];
 };
 
+struct Decomp;  // domain decomposition state of a grid (fd_decomp.cu)
+
 constexpr int kNumShapes = 5;
 extern const TileShape kShapes[kNumShapes];
 
@@ -113,6 +115,7 @@ struct fd_grid_s {
   bool graph_valid = false;
   cudaGraphExec_t gexec = nullptr;
   fd::GraphKey gkey = {};
+  fd::Decomp* dmp = nullptr;  // z slabs of fd_set_decomposition (nullptr: whole grid)
 };
 
 namespace fd {
@@ -122,6 +125,9 @@ fd_status cuda_fail(cudaError_t e, const char* what);
 void clear_error();
 cudaError_t dev_alloc(void** p, size_t bytes);
 bool is_device_ptr(const void* p);
+fd_status make_map(CUtensorMap* m, const float* base, int Nx, int Ny, int Nz, int pitch, int bx,
+                   int by);
+int radius_halo_x(int R);
 fd_status build_maps(fd_grid g);
 fd_status build_field_maps(fd_grid g, Fields& f);
 void set_shape(fd_grid g, TileShape t);
@@ -151,5 +157,10 @@ fd_status run_steps(fd_grid g, const RunSpec& rs);
 fd_status check_device_error(fd_grid g);
 fd_status check_finite(fd_grid g, const float* dev, size_t n);
 fd_status copy_field(fd_grid g, float* dev_field, void* user, int region, bool to_user);
+// decomposed runs (fd_decomp.cu): steps of fd_forward / fd_propagate when the
+// grid has slabs, and the release of the slabs with the grid
+fd_status decomp_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
+                           const float* wavelet, const fd_points* rec, float* rec_out);
+void decomp_destroy(fd_grid g);
 
 }  // namespace fd

@@ -332,7 +332,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     const float c0x3 = 3.0f * ov.c[0];
     // planes [zf_lo, zf_hi) of this column have b = 0 at every point and no
     // point outside the grid: there the update needs no sponge terms or masks
-    int zf_lo = a.nbl, zf_hi = a.nbl + a.nz;
+    int zf_lo = ov.nblz, zf_hi = ov.nblz + a.nz;
     {
       const bool no_sponge = a.bscale == 0.0f;
       const bool full = x0 + C::BX <= a.Nx && y0 + C::BY <= a.Ny;
@@ -469,7 +469,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             res[l] = fmaf(lane(Av, l), ls, fmaf(2.0f, lane(FD_Q(0), l), -lane(up, l)));
           }
         } else {
-          const int dz = sponge_depth(k, a.nbl, a.nz);
+          const int dz = sponge_depth(k, ov.nblz, a.nz);
           const float dzz = static_cast<float>(dz * dz);
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
@@ -600,8 +600,8 @@ __global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
     }
     __syncthreads();
     run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->C, sa, ov,
-                                    S->u[cur ^ 1], tile % sa.tiles_x, tile / sa.tiles_x, zb,
-                                    ze, smem);
+                                    S->u[cur ^ 1], tile % sa.tiles_x, tile / sa.tiles_x,
+                                    zb + ov.zfirst, ze + ov.zfirst, smem);
     __syncthreads();
     pos += ze - zb;
   }
