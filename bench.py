@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALGO_BYTES_PER_POINT = 16  # read u^n, u^{n-1}, A; write u^{n+1}
+_SCHED = {"auto": 0, "shares": 1, "waves": 2}
+_SCHED_NAME = {1: "shares", 2: "waves"}
 
 
 def _peaks():
@@ -219,6 +221,7 @@ def run_ours(args, w, world, rank, local):
         if args.tile:
             tx, ty, ctas = (int(v) for v in args.tile.split(","))
             g.set_tile(tx, ty, ctas)
+        g.set_schedule(_SCHED[args.sched])
         v_dev = torch.from_numpy(w["v"]).cuda()
         wav_dev = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
         rec_dev = torch.zeros((nt, nrec), device="cuda")
@@ -305,6 +308,7 @@ def run_ours(args, w, world, rank, local):
         "clocks": clk,
         "gpu_launches": int(launches),
         "tile": [info["tile_x"], info["tile_y"], info["ctas"]],
+        "schedule": _SCHED_NAME.get(info["schedule"]),
         "interior_gpts": world * int(np.prod(w["n"])) * nt * args.steps /
         (ms_max * 1e-3) / 1e9,
         "paper_context": {"value": 31.2, "unit": "Gpts/s",
@@ -425,7 +429,8 @@ def run_batched(args):
                       "data": "synthetic",
                       "config": {"workload": "32 shots 128..320^3 (+20) SO8 600 steps",
                                  "points": pts, "tile": [info["tile_x"], info["tile_y"],
-                                                         info["ctas"]]},
+                                                         info["ctas"]],
+                                 "schedule": _SCHED_NAME.get(info["schedule"])},
                       "sequential_gpts": pts * nt / (ms_s * 1e-3) / 1e9,
                       "speedup_vs_sequential": ms_s / ms_b,
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
@@ -631,6 +636,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--tile", default="", help="tile_x,tile_y,ctas for fd_set_tile")
     ap.add_argument("--space-order", type=int, default=8)
+    ap.add_argument("--sched", default="auto", choices=sorted(_SCHED),
+                    help="headline workload: work schedule of the step launches")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.workload != "headline":

@@ -92,6 +92,8 @@ typedef struct {
   int64_t launches;               /* library kernels launched so far */
   double step_ms;                 /* summed device time of profiled steps */
   int64_t steps_timed;            /* steps inside that time */
+  int32_t schedule;               /* of the last forward run: FD_SCHED_SHARES or
+                                     FD_SCHED_WAVES (0 before the first run) */
 } fd_grid_info;
 
 /* Creates a grid; allocates the two wavefields and the model on `device`.
@@ -221,6 +223,25 @@ fd_status fd_descent_step(int64_t n, float* m, const float* grad, double step,
  * the load of the busiest SM.
  * Errors: FD_ERR_ARG for a tile that is not compiled or ctas < 0. */
 fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas);
+
+/* How the persistent CTAs of a forward step share the grid's work units
+ * (one xy tile column over a range of z planes each):
+ *   FD_SCHED_SHARES  every resident CTA takes an equal contiguous share of
+ *                    the (tile, plane) units; when all tile columns fit in
+ *                    the resident CTAs, k equal z chunks per column instead
+ *                    (lockstep: all columns advance together and neighbours
+ *                    find each other's halo rows in L2);
+ *   FD_SCHED_WAVES   columns cut into z chunks of a common height, handed to
+ *                    the CTAs in waves of neighbouring chunks at the same
+ *                    depth, so neighbours share halos in L2 however many
+ *                    columns there are; the chunk height minimises the load
+ *                    of the busiest CTA (a host-side simulation);
+ *   FD_SCHED_AUTO    the library's default, currently FD_SCHED_SHARES.
+ * Adjoint and per-cell/table-weight steps always use equal shares; an
+ * explicit CTA count (fd_set_tile ctas > 0) does too.  Every schedule gives
+ * the same results bit for bit.  Errors: FD_ERR_ARG (unknown mode). */
+enum { FD_SCHED_AUTO = 0, FD_SCHED_SHARES = 1, FD_SCHED_WAVES = 2 };
+fd_status fd_set_schedule(fd_grid grid, int32_t mode);
 
 /* Test hooks, host-side fault injection only:
  *   FD_DEBUG_SKIP_PLANE  value z >= 0: the first step of the next run never

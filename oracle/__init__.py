@@ -8,7 +8,7 @@ meet only through the seeded input generators.
 Every function is a thin ctypes wrapper over ``fd_oracle.c`` (plain C, FP64),
 whose header lists the paper passages it follows and the readings taken where
 the paper is silent.  ``mlp.py`` holds the FP64 reference of the learned
-coefficient network.
+coefficient network, ``fwi.py`` that of the inversion loop's model update.
 
 Pinned: coefficients (moment conditions), the heat worked example (Sec. II,
 Listings 1-3), d'Alembert at Courant 1, plane-wave dispersion, energy balance

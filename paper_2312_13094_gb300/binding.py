@@ -37,6 +37,7 @@ FD_DEBUG_SKIP_PLANE, FD_DEBUG_SPIN_LIMIT, FD_DEBUG_NO_GRAPH = 1, 2, 3
 FD_COEF_TAYLOR, FD_COEF_UNIFORM, FD_COEF_PER_CELL = 0, 1, 2
 FD_MLP_NPARAM, FD_MLP_SAMPLE = 5000, 10
 FD_DMP_BASIC, FD_DMP_OVERLAP = 0, 1
+FD_SCHED_AUTO, FD_SCHED_SHARES, FD_SCHED_WAVES = 0, 1, 2
 
 
 class fd_grid_desc(ctypes.Structure):
@@ -56,7 +57,8 @@ class fd_grid_info(ctypes.Structure):
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("ctas", ctypes.c_int32), ("v_max", ctypes.c_double),
                 ("cfl_limit", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("step_ms", ctypes.c_double), ("steps_timed", ctypes.c_int64)]
+                ("step_ms", ctypes.c_double), ("steps_timed", ctypes.c_int64),
+                ("schedule", ctypes.c_int32)]
 
 
 class fd_shot(ctypes.Structure):
@@ -101,6 +103,7 @@ _SIGS = {
                                 _PTS, _P]),
     "fd_set_tile": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_decomposition": (_S, [_G, ctypes.c_int32, ctypes.c_int32]),
+    "fd_set_schedule": (_S, [_G, ctypes.c_int32]),
     "fd_descent_step": (_S, [ctypes.c_int64, _P, _P, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "fd_set_debug": (_S, [_G, ctypes.c_int32, ctypes.c_int64]),
@@ -223,6 +226,9 @@ class Grid:
 
     def set_tile(self, tile_x, tile_y, ctas=0):
         check(fd_set_tile(self.handle, tile_x, tile_y, ctas), "fd_set_tile")
+
+    def set_schedule(self, mode):
+        check(fd_set_schedule(self.handle, mode), "fd_set_schedule")
 
     def set_decomposition(self, nsub, mode=FD_DMP_BASIC):
         check(fd_set_decomposition(self.handle, nsub, mode), "fd_set_decomposition")

@@ -1,8 +1,9 @@
 // Batched multi-shot forward modelling: every time step of all shots is one
 // persistent sweep launch over the concatenated (shot, tile, plane) units of
-// the batch, each resident CTA taking an equal contiguous share, and the nt
-// launches are captured in one CUDA graph.  A tile autotuner times the
-// compiled tile shapes on the actual batch once per (GPU, space order, window
+// the batch, each resident CTA taking an equal contiguous share or running
+// the items of a column-wave schedule (fd_sched.cu), and the nt launches are
+// captured in one CUDA graph.  An autotuner times the compiled tile shapes
+// under both schedules on the actual batch once per (GPU, space order, window
 // sizes) and caches the pick in memory and, if FD_AUTOTUNE_CACHE names a
 // file, on disk (the paper tunes loop blocking the same way, Sec. IV-C).
 #include <string.h>
@@ -15,6 +16,7 @@
 
 #include "fd_aux.h"
 #include "fd_runtime.h"
+#include "fd_sched.h"
 
 using namespace fd;
 
@@ -29,7 +31,11 @@ struct BatchWorkspace {
 
 std::mutex g_mu;
 std::map<int, BatchWorkspace> g_ws;        // per device
-std::map<std::string, TileShape> g_tuned;  // autotuner picks
+struct Pick {
+  TileShape t;
+  bool waves;  // wave schedule instead of equal shares
+};
+std::map<std::string, Pick> g_tuned;  // autotuner picks
 
 std::string tune_key(int device, int R, int nshots, const fd_shot* shots) {
   cudaDeviceProp p;
@@ -41,7 +47,7 @@ std::string tune_key(int device, int R, int nshots, const fd_shot* shots) {
                    std::to_string(g->Nz));
   }
   std::sort(dims.begin(), dims.end());
-  std::string k = std::string(p.name) + "|R" + std::to_string(R);
+  std::string k = std::string(p.name) + "|v2|R" + std::to_string(R);
   for (auto& d : dims) k += "|" + d;
   for (auto& c : k)
     if (c == ' ') c = '_';
@@ -56,27 +62,33 @@ void load_cache_file() {
   if (!path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char key[4096];
+  char line[8192], key[4096];
   TileShape t;
-  while (fscanf(f, "%4095s %d %d %d %d", key, &t.tx, &t.ty, &t.pf, &t.ctas) == 5)
-    g_tuned[key] = t;
+  int waves = 0;
+  while (fgets(line, sizeof(line), f)) {
+    if (sscanf(line, "%4095s %d %d %d %d %d", key, &t.tx, &t.ty, &t.pf, &t.ctas, &waves) == 6)
+      g_tuned[key] = {t, waves != 0};
+  }
   fclose(f);
 }
 
-void save_cache_entry(const std::string& key, const TileShape& t) {
+void save_cache_entry(const std::string& key, const Pick& p) {
   const char* path = getenv("FD_AUTOTUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.tx, t.ty, t.pf, t.ctas);
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), p.t.tx, p.t.ty, p.t.pf, p.t.ctas,
+          p.waves ? 1 : 0);
   fclose(f);
 }
 
 struct Prepared {
-  std::vector<char> host;  // descriptors + prefix, as uploaded
+  std::vector<char> host;  // descriptors + prefix (+ wave schedule), as uploaded
   std::vector<float*> drec;
   int nshots = 0;
   int ctas = 0;
+  bool waves = false;
+  size_t off_start = 0, off_items = 0;  // wave schedule within `host`
   float c[kMaxR + 1] = {};  // stencil weights (the same for every shot)
   int nbl = 0;              // layer width (the same for every shot)
   long long spin_limit = 0;
@@ -84,7 +96,8 @@ struct Prepared {
 
 // Puts every shot on tile shape t and builds the descriptors and the unit
 // prefix of the batch.
-fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared& P) {
+fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, bool waves,
+                  Prepared& P) {
   const int R = shots[0].grid->R;
   P.nshots = nshots;
   P.drec.assign(nshots, nullptr);
@@ -132,6 +145,25 @@ fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, Prepared
     prefix[i + 1] = prefix[i] + (long long)g->tiles_x * g->tiles_y * g->Nz;
   }
   P.ctas = sweep_ctas(R, t, kModeForward);
+  P.waves = waves;
+  if (waves) {
+    // taller windows first, so that a wave holds chunks of similar height
+    std::vector<SchedGrid> grids;
+    for (int i = 0; i < nshots; ++i) {
+      fd_grid g = shots[i].grid;
+      grids.push_back({i, g->tiles_x * g->tiles_y, g->Nz});
+    }
+    std::stable_sort(grids.begin(), grids.end(),
+                     [](const SchedGrid& a, const SchedGrid& b) { return a.nz > b.nz; });
+    std::vector<int32_t> start;
+    std::vector<WorkItem> items;
+    P.ctas = wave_schedule(grids, P.ctas, R, start, items);
+    P.off_start = (P.host.size() + 15) / 16 * 16;
+    P.off_items = (P.off_start + start.size() * 4 + 15) / 16 * 16;
+    P.host.resize(P.off_items + items.size() * sizeof(WorkItem), 0);
+    memcpy(P.host.data() + P.off_start, start.data(), start.size() * 4);
+    memcpy(P.host.data() + P.off_items, items.data(), items.size() * sizeof(WorkItem));
+  }
   fd_grid g0 = shots[0].grid;
   for (int j = 0; j <= kMaxR; ++j) P.c[j] = j <= R ? float(g0->c[j]) : 0.0f;
   P.spin_limit = g0->spin_limit;
@@ -177,6 +209,11 @@ fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileSh
     ov.spin_limit = P.spin_limit;
     ov.debug_skip_plane = -1;
     for (int j = 0; j <= kMaxR; ++j) ov.c[j] = P.c[j];
+    if (P.waves) {
+      const char* base = static_cast<const char*>(ws.desc.p);
+      ov.item_start = reinterpret_cast<const int32_t*>(base + P.off_start);
+      ov.items = reinterpret_cast<const WorkItem*>(base + P.off_items);
+    }
     cudaError_t e = launch_sweep(R, t, kModeForward, d, prefix, P.nshots, ov, P.ctas, s);
     if (e) return cuda_fail(e, "batch launch");
   }
@@ -184,17 +221,18 @@ fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileSh
 }
 
 fd_status autotune(BatchWorkspace& ws, int nshots, const fd_shot* shots, int R, int nt,
-                   cudaStream_t s, TileShape* best) {
+                   cudaStream_t s, Pick* best) {
   const int trial = std::max(1, std::min(nt, 6));
   float best_ms = 1e30f;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   fd_status st = FD_OK;
-  for (int i = 0; i < kNumShapes && !st; ++i) {
-    TileShape t = kShapes[i];
+  for (int c = 0; c < 2 * kNumShapes && !st; ++c) {
+    TileShape t = kShapes[c / 2];
+    const bool waves = (c & 1) != 0;
     Prepared P;
-    st = prepare(nshots, shots, t, P);
+    st = prepare(nshots, shots, t, waves, P);
     if (!st) st = upload_prepared(ws, P, s);
     if (!st) st = zero_state(nshots, shots, s);
     if (!st) st = issue_steps(ws, P, R, t, 1, s);  // warm-up
@@ -211,7 +249,7 @@ fd_status autotune(BatchWorkspace& ws, int nshots, const fd_shot* shots, int R, 
     cudaEventElapsedTime(&ms, a, b);
     if (ms < best_ms) {
       best_ms = ms;
-      *best = t;
+      *best = {t, waves};
     }
   }
   cudaEventDestroy(a);
@@ -252,21 +290,22 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
   BatchWorkspace& ws = g_ws[g0->d.device];
 
   // tile shape: autotuned (cached), else the single-grid default
-  TileShape t = default_shape(R, g0->Nx, g0->Ny, g0->Nz);
+  Pick pick = {default_shape(R, g0->Nx, g0->Ny, g0->Nz), g0->sched_mode == FD_SCHED_WAVES};
   load_cache_file();
   const std::string key = tune_key(g0->d.device, R, nshots, shots);
   auto it = g_tuned.find(key);
   fd_status st;
   if (it != g_tuned.end()) {
-    t = it->second;
+    pick = it->second;
   } else if (flags & FD_BATCH_AUTOTUNE) {
-    if ((st = autotune(ws, nshots, shots, R, nt, s, &t))) return st;
-    g_tuned[key] = t;
-    save_cache_entry(key, t);
+    if ((st = autotune(ws, nshots, shots, R, nt, s, &pick))) return st;
+    g_tuned[key] = pick;
+    save_cache_entry(key, pick);
   }
+  const TileShape t = pick.t;
 
   Prepared P;
-  if ((st = prepare(nshots, shots, t, P))) return st;
+  if ((st = prepare(nshots, shots, t, pick.waves, P))) return st;
   if ((st = upload_prepared(ws, P, s))) return st;
   if ((st = zero_state(nshots, shots, s))) return st;
 
@@ -278,7 +317,7 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
     char* q = key_bytes.data();
     memcpy(q, &t, sizeof(t));
     q += sizeof(t);
-    int ints[4] = {R, nt, P.nshots, P.ctas};
+    int ints[4] = {R, nt, P.nshots, P.ctas * 2 + (P.waves ? 1 : 0)};
     memcpy(q, ints, sizeof(ints));
     q += sizeof(ints);
     memcpy(q, &ws.desc.p, sizeof(void*));
@@ -324,6 +363,7 @@ extern "C" fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots, int3
   for (int i = 0; i < nshots; ++i) {
     fd_grid g = shots[i].grid;
     g->F.cur = nt & 1;
+    g->last_sched = pick.waves ? FD_SCHED_WAVES : FD_SCHED_SHARES;
     // every grid's error word and receivers were written on stream s
     cudaStream_t own = g->stream;
     g->stream = s;

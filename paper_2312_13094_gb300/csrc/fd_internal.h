@@ -80,6 +80,12 @@ struct ShotDesc {
   float* u[2];
 };
 
+// One work item of a scheduled sweep: planes [zb, ze) of tile column `tile`
+// of grid `shot` of the launch.
+struct WorkItem {
+  int32_t shot, tile, zb, ze;
+};
+
 // Per-launch values of a sweep: buffer parity, table rows, imaging fields.
 struct StepOverride {
   int cur;            // u[cur] holds u^n
@@ -94,6 +100,8 @@ struct StepOverride {
   const float* e_in;
   long long spin_limit;      // clock cycles before a wait gives up
   float c[kMaxR + 1];        // stencil weights shared by every shot of the launch
+  const int32_t* item_start; // scheduled sweep: CTA c runs items [item_start[c],
+  const WorkItem* items;     // item_start[c+1]); nullptr: equal contiguous shares
 };
 
 struct TileShape {

@@ -22,6 +22,7 @@
 #include "fd_internal.h"
 #include "fd_mlp.h"
 #include "fd_runtime.h"
+#include "fd_sched.h"
 
 namespace fd {
 
@@ -518,6 +519,42 @@ void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d) {
   d->args.out = nullptr;
 }
 
+// FD_SCHED_AUTO keeps the equal-share sweep (and lockstep when the columns
+// fit); FD_SCHED_WAVES runs every forward sweep of the grid on the wave
+// schedule of fd_sched.cu.
+int grid_schedule(fd_grid g, int mode, StepOverride* ov, fd_status* st) {
+  *st = FD_OK;
+  if (mode != kModeForward || g->shape.ctas > 0 || g->sched_mode != FD_SCHED_WAVES) return 0;
+  const int slots = sweep_ctas(g->R, g->shape, mode);
+  const long long key[5] = {g->shape.tx, g->shape.ty, g->Nz,
+                            (long long)g->tiles_x * g->tiles_y, slots};
+  if (memcmp(key, g->sched_key, sizeof(key)) != 0 || !g->sched.p) {
+    std::vector<int32_t> start;
+    std::vector<WorkItem> items;
+    const std::vector<SchedGrid> grids = {{0, g->tiles_x * g->tiles_y, g->Nz}};
+    const int used = wave_schedule(grids, slots, g->R, start, items);
+    const size_t off = (start.size() * 4 + 15) / 16 * 16;
+    cudaError_t e = g->sched.ensure(off + items.size() * sizeof(WorkItem));
+    if (!e) e = cudaMemcpyAsync(g->sched.p, start.data(), start.size() * 4,
+                                cudaMemcpyHostToDevice, g->stream);
+    if (!e)
+      e = cudaMemcpyAsync(static_cast<char*>(g->sched.p) + off, items.data(),
+                          items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, g->stream);
+    if (!e) e = cudaStreamSynchronize(g->stream);
+    if (e) {
+      *st = cuda_fail(e, "schedule upload");
+      return 0;
+    }
+    memcpy(g->sched_key, key, sizeof(key));
+    g->sched_ctas = used;
+    g->sched_off = off;
+  }
+  ov->item_start = static_cast<const int32_t*>(g->sched.p);
+  ov->items = reinterpret_cast<const WorkItem*>(static_cast<const char*>(g->sched.p) +
+                                                g->sched_off);
+  return g->sched_ctas;
+}
+
 fd_status run_steps(fd_grid g, const RunSpec& rs) {
   if (rs.nsteps <= 0) return FD_OK;
   cudaError_t e;
@@ -529,6 +566,15 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   // neighbours, which share halos in L2; otherwise equal contiguous shares
   // of all the (tile, plane) units over every resident slot
   int G = lockstep_ctas(g->R, g->shape, mode, (long long)g->tiles_x * g->tiles_y, g->Nz);
+  StepOverride sched_ov;
+  memset(&sched_ov, 0, sizeof(sched_ov));
+  {
+    fd_status st = FD_OK;
+    const int Gs = grid_schedule(g, mode, &sched_ov, &st);
+    if (st) return st;
+    if (Gs > 0) G = Gs;
+    if (mode == kModeForward) g->last_sched = Gs > 0 ? FD_SCHED_WAVES : FD_SCHED_SHARES;
+  }
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
   struct {
@@ -564,6 +610,7 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   key.shape = g->shape;
   key.ctas = G;
   key.desc = dslot;
+  key.sched = sched_ov.items;
   key.skip = g->debug_skip_plane;
   key.spin = g->spin_limit;
   for (int j = 0; j <= kMaxR; ++j) key.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
@@ -586,6 +633,8 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       ov.cur = (cur0 + t) & 1;
       ov.zfirst = 0;
       ov.nblz = g->d.nbl;
+      ov.item_start = sched_ov.item_start;
+      ov.items = sched_ov.items;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
       for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
@@ -798,7 +847,7 @@ fd_status fd_destroy_grid(fd_grid g) {
                     &g->tab_adj.inj_start, &g->tab_adj.inj, &g->tab_adj.rec_start,
                     &g->tab_adj.recs,
                     &g->stage_val, &g->stage_rec, &g->stage_aux, &g->ckpt, &g->ebuf,
-                    &g->gpad, &g->resid, &g->recbuf, &g->desc})
+                    &g->gpad, &g->resid, &g->recbuf, &g->desc, &g->sched})
     b->release();
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
@@ -980,6 +1029,7 @@ fd_status fd_get_info(fd_grid g, fd_grid_info* info) {
   info->launches = g_launches.load();
   info->step_ms = g->step_ms;
   info->steps_timed = g->steps_timed;
+  info->schedule = g->last_sched;
   return FD_OK;
 }
 
@@ -1105,6 +1155,16 @@ fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t ctas) {
     }
   }
   return fail(FD_ERR_ARG, "tile %dx%d is not compiled", tile_x, tile_y);
+}
+
+fd_status fd_set_schedule(fd_grid g, int32_t mode) {
+  clear_error();
+  if (!g) return fail(FD_ERR_ARG, "null grid");
+  if (mode != FD_SCHED_AUTO && mode != FD_SCHED_SHARES && mode != FD_SCHED_WAVES)
+    return fail(FD_ERR_ARG, "bad schedule %d", mode);
+  g->sched_mode = mode;
+  g->graph_valid = false;
+  return FD_OK;
 }
 
 fd_status fd_set_debug(fd_grid g, int32_t key, int64_t value) {

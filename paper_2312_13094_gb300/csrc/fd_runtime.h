@@ -61,6 +61,7 @@ struct GraphKey {
   TileShape shape;
   int ctas;
   void* desc;
+  const void* sched;  // work items of a wave-scheduled sweep (nullptr: equal shares)
   int skip;
   long long spin;
   float c[kMaxR + 1];
@@ -116,6 +117,12 @@ struct fd_grid_s {
   cudaGraphExec_t gexec = nullptr;
   fd::GraphKey gkey = {};
   fd::Decomp* dmp = nullptr;  // z slabs of fd_set_decomposition (nullptr: whole grid)
+  int sched_mode = FD_SCHED_AUTO;  // fd_set_schedule
+  fd::DevBuf sched;                // wave schedule: CTA starts, then the work items
+  long long sched_key[5] = {};     // tile, grid and CTA count it was built for
+  int sched_ctas = 0;              // CTAs of the wave-scheduled launch
+  size_t sched_off = 0;            // byte offset of the items in g->sched
+  int last_sched = 0;              // schedule of the last forward run (fd_grid_info)
 };
 
 namespace fd {
@@ -154,6 +161,10 @@ fd_status stage_in(fd_grid g, DevBuf& buf, const float* p, size_t n, const float
 fd_status stage_out(fd_grid g, DevBuf& buf, float* p, size_t n, float** out);
 fd_status finish_out(fd_grid g, float* host, const float* dev, size_t n);
 fd_status run_steps(fd_grid g, const RunSpec& rs);
+// Wave schedule of the grid's forward sweeps (built once per tile shape and
+// CTA count, uploaded to g->sched); fills the item pointers of a launch and
+// returns its CTA count, or 0 when the grid runs equal shares.
+int grid_schedule(fd_grid g, int mode, StepOverride* ov, fd_status* st);
 fd_status check_device_error(fd_grid g);
 fd_status check_finite(fd_grid g, const float* dev, size_t n);
 fd_status copy_field(fd_grid g, float* dev_field, void* user, int region, bool to_user);

@@ -568,7 +568,9 @@ fail:
 // units of shots 0..s-1; CTA c of G takes the contiguous share
 // [c*total/G, (c+1)*total/G), cut into per-tile z segments.  With G equal to
 // the number of resident CTAs every SM streams the same number of planes and
-// no CTA waits for a second wave.
+// no CTA waits for a second wave.  A scheduled sweep (ov.items set) instead
+// runs the host-built work items [item_start[c], item_start[c+1]) of CTA c:
+// z ranges of tile columns in any order (column waves, see fd_sched.cu).
 template <int R, int TX, int TY, int PF, int MODE>
 __global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
     sweep_kernel(const ShotDesc* __restrict__ shots, const long long* __restrict__ prefix,
@@ -604,6 +606,37 @@ __global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
                                     zb + ov.zfirst, ze + ov.zfirst, smem);
     __syncthreads();
     pos += ze - zb;
+  }
+}
+
+// Scheduled sweep: CTA c runs the host-built work items
+// [ov.item_start[c], ov.item_start[c+1]) in order, each the planes [zb, ze)
+// of one tile column of one grid (column waves, fd_sched.cu).  A kernel of
+// its own, so that the equal-share sweep above keeps its register allocation.
+template <int R, int TX, int TY, int PF, int MODE>
+__global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
+    sched_kernel(const ShotDesc* __restrict__ shots, const __grid_constant__ StepOverride ov) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  __shared__ StepArgs sa;
+  const int cur = ov.cur;
+  const int i1 = ov.item_start[blockIdx.x + 1];
+  for (int i = ov.item_start[blockIdx.x]; i < i1; ++i) {
+    const WorkItem w = ov.items[i];
+    const ShotDesc* S = shots + w.shot;
+    if (threadIdx.x == 0) {
+      sa = S->args;
+      sa.inj_row = ov.inj_row;
+      sa.rec_row = ov.rec_row;
+      sa.e_out = ov.e_out;
+      sa.e_in = ov.e_in;
+    }
+    __syncthreads();
+    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->C, sa, ov,
+                                    S->u[cur ^ 1], w.tile % sa.tiles_x, w.tile / sa.tiles_x,
+                                    w.zb + ov.zfirst, w.ze + ov.zfirst, smem);
+    __syncthreads();
   }
 }
 

@@ -31,9 +31,35 @@ cudaError_t set_smem_attr() {
   return e;
 }
 
+// The scheduled sweep (forward mode only): the same shared memory and launch
+// bounds as the equal-share kernel, so the same CTAs fit on an SM.
+template <int R, int TX, int TY, int PF>
+cudaError_t set_sched_smem_attr() {
+  static unsigned long long done = 0;  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (done & (1ull << (dev & 63))) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(sched_kernel<R, TX, TY, PF, kModeForward>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       sweep_smem<R, TX, TY, PF, kModeForward>());
+  if (e == cudaSuccess) done |= 1ull << (dev & 63);
+  return e;
+}
+
 template <int R, int TX, int TY, int PF, int MODE>
 cudaError_t launch_one(const ShotDesc* shots, const long long* prefix, int nshots,
                        const StepOverride& ov, int grid, cudaStream_t s) {
+  if (ov.items) {
+    if constexpr (MODE == kModeForward) {
+      cudaError_t e = set_sched_smem_attr<R, TX, TY, PF>();
+      if (e != cudaSuccess) return e;
+      sched_kernel<R, TX, TY, PF, MODE><<<grid, TX * TY, sweep_smem<R, TX, TY, PF, MODE>(), s>>>(
+          shots, ov);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   cudaError_t e = set_smem_attr<R, TX, TY, PF, MODE>();
   if (e != cudaSuccess) return e;
   sweep_kernel<R, TX, TY, PF, MODE><<<grid, TX * TY, sweep_smem<R, TX, TY, PF, MODE>(), s>>>(
