@@ -59,18 +59,20 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload, tile):
+def _traffic(workload, tile, schedule):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source with the same tile; else None."""
+    if it was taken on the current kernel source with the same tile and
+    schedule; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(workload)
-    if not e or e.get("kernel_hash") != _kernel_hash() or list(e.get("tile", [])) != list(tile):
-        return None
-    return e.get("dram_bytes_per_launch")
+    for e in d.get(workload, []):
+        if (e.get("kernel_hash") == _kernel_hash() and list(e.get("tile", [])) == list(tile)
+                and e.get("schedule") == schedule):
+            return e.get("dram_bytes_per_launch")
+    return None
 
 
 class ClockSampler:
@@ -301,8 +303,10 @@ def run_ours(args, w, world, rank, local):
         "data": "synthetic", "config": _config(w),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": _traffic(w["name"], [info["tile_x"], info["tile_y"]]),
-                     "kernel": "fd::sweep_kernel (avg over the timed launches)",
+                     "traffic": _traffic(w["name"], [info["tile_x"], info["tile_y"]],
+                                         _SCHED_NAME.get(info["schedule"])),
+                     "kernel": ("fd::sched_kernel" if info["schedule"] == 2 else
+                                "fd::sweep_kernel") + " (avg over the timed launches)",
                      "algorithmic_bytes_per_launch": ALGO_BYTES_PER_POINT * npts,
                      "avg_launch_ms": avg_launch_ms},
         "clocks": clk,
@@ -454,6 +458,10 @@ def run_decomposed(args):
     peak, kind = _peaks()
     with torch.cuda.stream(stream):
         g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
+        # slabs run the default tile with equal shares: keep the whole grid
+        # on the same (no tuning), so the rows differ only by the slabs
+        i0 = g.info()
+        g.set_tile(i0["tile_x"], i0["tile_y"], 0)
         v_dev = torch.from_numpy(w["v"]).cuda()
         wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
         rec = torch.zeros((nt, len(w["rec"])), device="cuda")

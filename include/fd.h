@@ -214,7 +214,8 @@ fd_status fd_descent_step(int64_t n, float* m, const float* grad, double step,
                           double* alpha_out);
 
 /* Chooses the stencil tile (tile_x x tile_y points per CTA column) and the
- * number of persistent CTAs of each step launch.  Each CTA sweeps an equal
+ * number of persistent CTAs of each step launch (and turns off the tuning
+ * of FD_SCHED_AUTO for this grid).  Each CTA sweeps an equal
  * contiguous share of the grid's (tile, z plane) units.  ctas = 0 picks the
  * count: when all tile columns fit in the CTAs resident at once, k equal z
  * chunks per column (all columns advance together and share halos in L2),
@@ -236,10 +237,20 @@ fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas
  *                    depth, so neighbours share halos in L2 however many
  *                    columns there are; the chunk height minimises the load
  *                    of the busiest CTA (a host-side simulation);
- *   FD_SCHED_AUTO    the library's default, currently FD_SCHED_SHARES.
- * Adjoint and per-cell/table-weight steps always use equal shares; an
- * explicit CTA count (fd_set_tile ctas > 0) does too.  Every schedule gives
- * the same results bit for bit.  Errors: FD_ERR_ARG (unknown mode). */
+ *   FD_SCHED_AUTO    the default: equal shares, except that a grid left on
+ *                    its default tile (no fd_set_tile call) is tuned by its
+ *                    first fd_forward of at least 400 steps: every compiled
+ *                    tile is timed under both schedules for a few
+ *                    source-free steps on the zeroed wavefields (cleared
+ *                    again before the run), and the fastest pair serves all
+ *                    later plain forward runs of grids of that padded size
+ *                    on that device (fd_forward and fd_propagate; the pick is
+ *                    cached per process; fd_grid_info shows the tile and
+ *                    schedule in use).
+ * Adjoint and per-cell/table-weight steps always use equal shares on the
+ * default tile; an explicit CTA count (fd_set_tile ctas > 0) uses equal
+ * shares too.  Every schedule and tile gives the same results bit for bit.
+ * Errors: FD_ERR_ARG (unknown mode). */
 enum { FD_SCHED_AUTO = 0, FD_SCHED_SHARES = 1, FD_SCHED_WAVES = 2 };
 fd_status fd_set_schedule(fd_grid grid, int32_t mode);
 

@@ -48,6 +48,12 @@ fd_status copy_async(fd_grid g, void* dst, const void* src, size_t bytes) {
 fd_status adjoint_impl(fd_grid g, const fd_points* src, const float* wavelet,
                        const fd_points* rec, const float* d_obs, const float* resid_in,
                        int32_t n_checkpoints, float* grad_m, double* loss_out) {
+  {
+    // the adjoint's launches run on the base tile, whatever the tuner picked
+    // for plain forward runs
+    fd_status st0 = use_shape(g, false);
+    if (st0) return st0;
+  }
   if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
   if (g->percell || g->table_mode)
     return fail(FD_ERR_STATE, "the adjoint is built for the symmetric uniform-weight stencil");

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -519,12 +521,16 @@ void fill_desc(fd_grid g, const RunSpec& rs, ShotDesc* d) {
   d->args.out = nullptr;
 }
 
-// FD_SCHED_AUTO keeps the equal-share sweep (and lockstep when the columns
-// fit); FD_SCHED_WAVES runs every forward sweep of the grid on the wave
-// schedule of fd_sched.cu.
+// FD_SCHED_WAVES runs every forward sweep of the grid on the wave schedule of
+// fd_sched.cu; FD_SCHED_AUTO does so for plain forward runs when the tuner
+// picked it, else the equal-share sweep (lockstep when the columns fit).
 int grid_schedule(fd_grid g, int mode, StepOverride* ov, fd_status* st) {
   *st = FD_OK;
-  if (mode != kModeForward || g->shape.ctas > 0 || g->sched_mode != FD_SCHED_WAVES) return 0;
+  const bool tuned_waves = g->sched_mode == FD_SCHED_AUTO && g->tuned && g->tuned_waves &&
+                           g->shape.tx == g->tuned_shape.tx && g->shape.ty == g->tuned_shape.ty;
+  if (mode != kModeForward || g->shape.ctas > 0 ||
+      !(g->sched_mode == FD_SCHED_WAVES || tuned_waves))
+    return 0;
   const int slots = sweep_ctas(g->R, g->shape, mode);
   const long long key[5] = {g->shape.tx, g->shape.ty, g->Nz,
                             (long long)g->tiles_x * g->tiles_y, slots};
@@ -553,6 +559,93 @@ int grid_schedule(fd_grid g, int mode, StepOverride* ov, fd_status* st) {
   ov->items = reinterpret_cast<const WorkItem*>(static_cast<const char*>(g->sched.p) +
                                                 g->sched_off);
   return g->sched_ctas;
+}
+
+fd_status use_shape(fd_grid g, bool plain_forward) {
+  const TileShape want = (plain_forward && g->tuned && g->sched_mode == FD_SCHED_AUTO)
+                             ? g->tuned_shape
+                             : g->base_shape;
+  if (want.tx == 0) return FD_OK;  // a grid without a base tile keeps its own
+  if (want.tx == g->shape.tx && want.ty == g->shape.ty && want.ctas == g->shape.ctas)
+    return FD_OK;
+  set_shape(g, want);
+  return build_maps(g);
+}
+
+// Tuner picks per (device, radius, padded size).
+static std::mutex g_tune_mu;
+static std::map<std::string, std::pair<TileShape, bool>> g_tune_cache;
+
+fd_status autotune_grid(fd_grid g) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, g->d.device);
+  const std::string key = std::string(prop.name) + "|R" + std::to_string(g->R) + "|" +
+                          std::to_string(g->Nx) + "x" + std::to_string(g->Ny) + "x" +
+                          std::to_string(g->Nz);
+  std::pair<TileShape, bool> pick = {g->base_shape, false};
+  bool found = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      pick = it->second;
+      found = true;
+    }
+  }
+  fd_status st = FD_OK;
+  if (!found) {
+    const bool prof = g->profiling;
+    g->profiling = false;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (!e) e = cudaEventCreate(&b);
+    if (e) st = cuda_fail(e, "tuner events");
+    RunSpec rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.f = &g->F;
+    rs.allow_graph = 0;
+    rs.mode = kModeForward;
+    const int trial = 6;
+    float best = 1e30f;
+    for (int c = 0; c < 2 * kNumShapes && !st; ++c) {
+      const TileShape t = kShapes[c / 2];
+      g->tuned = true;
+      g->tuned_shape = t;
+      g->tuned_waves = (c & 1) != 0;
+      if ((st = use_shape(g, true))) break;
+      rs.nsteps = 1;  // warm-up (builds the schedule)
+      if ((st = run_steps(g, rs))) break;
+      cudaEventRecord(a, g->stream);
+      rs.nsteps = trial;
+      if ((st = run_steps(g, rs))) break;
+      cudaEventRecord(b, g->stream);
+      if ((e = cudaEventSynchronize(b))) {
+        st = cuda_fail(e, "tuner timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        pick = {t, g->tuned_waves};
+      }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    g->profiling = prof;
+    if (!st) st = check_device_error(g);
+    if (st) {
+      g->tuned = false;
+      use_shape(g, false);
+      return st;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = pick;
+  }
+  g->tuned = true;
+  g->tuned_shape = pick.first;
+  g->tuned_waves = pick.second;
+  return use_shape(g, true);
 }
 
 fd_status run_steps(fd_grid g, const RunSpec& rs) {
@@ -787,6 +880,8 @@ fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
   g->spin_limit = 200000000LL;  // ~0.1 s at 2 GHz; a tile load takes microseconds
   if (const char* s = getenv("FD_SPIN_LIMIT")) g->spin_limit = atoll(s);
   set_shape(g, default_shape(g->R, g->Nx, g->Ny, g->Nz));
+  g->base_shape = g->shape;
+  g->auto_tile = true;
 
   fd_status st = FD_OK;
   if (d->stream) {
@@ -909,8 +1004,10 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
   const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;
   if ((nsrc && (!src->xyz || !wavelet)) || (nrec && (!rec->xyz || !rec_out)))
     return fail(FD_ERR_ARG, "points given without their data array");
+  fd_status st = use_shape(g, !g->dmp && forward_mode(g) == kModeForward);
+  if (st) return st;
   if (g->dmp) return decomp_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
-  fd_status st = upload_tables(g, src, 1.0 / g->d.h, rec, g->tab);
+  st = upload_tables(g, src, 1.0 / g->d.h, rec, g->tab);
   if (st) return st;
   const float* dval = nullptr;
   float* drec = nullptr;
@@ -973,6 +1070,18 @@ fd_status fd_forward(fd_grid g, const fd_points* src, const float* wavelet,
     if (e) return cuda_fail(e, "wavefield reset");
   }
   g->F.cur = 0;
+  // plain forward runs of grids left on the default tile are tuned once, on
+  // the zeroed wavefields, which are cleared again afterwards
+  if (g->auto_tile && !g->tuned && g->sched_mode == FD_SCHED_AUTO && !g->dmp &&
+      forward_mode(g) == kModeForward && g->d.nt >= kTuneMinSteps && g->debug_skip_plane < 0) {
+    fd_status st = autotune_grid(g);
+    if (st) return st;
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMemsetAsync(g->F.u[b], 0, g->ncell * 4, g->stream);
+      if (e) return cuda_fail(e, "wavefield reset");
+    }
+    g->F.cur = 0;
+  }
   fd_status st = propagate_impl(g, 0, g->d.nt, src, wavelet, rec, rec_out);
   if (st) return st;
   if (u_out) {
@@ -1151,6 +1260,9 @@ fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t ctas) {
       TileShape t = kShapes[i];
       t.ctas = ctas;
       set_shape(g, t);
+      g->base_shape = t;
+      g->auto_tile = false;
+      g->tuned = false;
       return build_maps(g);
     }
   }

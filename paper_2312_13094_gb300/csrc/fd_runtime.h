@@ -70,6 +70,7 @@ struct GraphKey {
 struct Decomp;  // domain decomposition state of a grid (fd_decomp.cu)
 
 constexpr int kNumShapes = 5;
+constexpr int kTuneMinSteps = 400;  // shorter forward runs are not worth tuning
 extern const TileShape kShapes[kNumShapes];
 
 }  // namespace fd
@@ -123,6 +124,11 @@ struct fd_grid_s {
   int sched_ctas = 0;              // CTAs of the wave-scheduled launch
   size_t sched_off = 0;            // byte offset of the items in g->sched
   int last_sched = 0;              // schedule of the last forward run (fd_grid_info)
+  fd::TileShape base_shape = {};   // tile of every run but tuned forward runs
+  bool auto_tile = false;          // no fd_set_tile: plain forward runs may be tuned
+  bool tuned = false;              // tuned_shape / tuned_waves hold the tuner's pick
+  fd::TileShape tuned_shape = {};
+  bool tuned_waves = false;
 };
 
 namespace fd {
@@ -138,6 +144,13 @@ int radius_halo_x(int R);
 fd_status build_maps(fd_grid g);
 fd_status build_field_maps(fd_grid g, Fields& f);
 void set_shape(fd_grid g, TileShape t);
+// Puts the grid on the tile its next run uses: the tuned one for plain forward
+// runs of a tuned grid, else the base tile (rebuilding the tensor maps).
+fd_status use_shape(fd_grid g, bool plain_forward);
+// Times every compiled tile under both schedules on the grid's zeroed
+// wavefields (a few source-free steps each) and records the fastest for plain
+// forward runs; picks are cached per device and padded size.
+fd_status autotune_grid(fd_grid g);
 TileShape default_shape(int R, int Nx, int Ny, int Nz);
 cudaError_t launch_sweep(int R, const TileShape& t, int mode, const ShotDesc* shots,
                          const long long* prefix, int nshots, const StepOverride& ov, int grid,

@@ -104,3 +104,46 @@ def test_unknown_schedule_is_rejected(fd):
         with pytest.raises(fd.FDError) as e:
             g.set_schedule(7)
         assert e.value.status == fd.FD_ERR_ARG
+
+
+def test_tuner_keeps_the_bits_and_the_adjoint_keeps_its_tile(fd):
+    """A grid left on its default tile is tuned by its first long fd_forward:
+    the pick is a compiled tile under one of the two schedules, the receivers
+    and wavefield equal an untuned run on the default tile bit for bit, and a
+    later adjoint gradient equals that of a grid that was never tuned."""
+    import torch
+    w = workload(8, (60, 50, 44), 6, 420)
+    rec0 = np.zeros((w["nt"], len(w["rec"])), np.float32)
+    u0 = np.zeros((44, 50, 60), np.float32)
+    g0 = torch.zeros((44, 50, 60), device="cuda")
+    with fd.Grid.from_workload(w) as g:
+        i0 = g.info()
+        g.set_tile(i0["tile_x"], i0["tile_y"], 0)  # tuning off, default tile
+        g.set_model(w["v"])
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec0, u0), "fd_forward")
+        assert g.info()["schedule"] == fd.FD_SCHED_SHARES
+        st, loss0 = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], 0.5 * rec0, 5, g0)
+        fd.check(st, "fd_adjoint_gradient")
+    rec1 = np.zeros_like(rec0)
+    u1 = np.zeros_like(u0)
+    g1 = torch.zeros_like(g0)
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(w["v"])
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec1, u1), "fd_forward")
+        info = g.info()
+        assert (info["tile_x"], info["tile_y"]) in [(64, 16), (128, 8), (32, 16), (64, 8),
+                                                    (32, 8)]
+        assert info["schedule"] in (fd.FD_SCHED_SHARES, fd.FD_SCHED_WAVES)
+        st, loss1 = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], 0.5 * rec0, 5, g1)
+        fd.check(st, "fd_adjoint_gradient")
+        # the tuned pair serves the next forward run again
+        rec2 = np.zeros_like(rec0)
+        fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec2), "fd_forward")
+        assert (g.info()["tile_x"], g.info()["tile_y"]) == (info["tile_x"], info["tile_y"])
+    np.testing.assert_array_equal(rec0, rec1)
+    np.testing.assert_array_equal(u0, u1)
+    np.testing.assert_array_equal(rec2, rec0)
+    # the misfit is a double sum accumulated with atomics: equal up to the
+    # order of the additions
+    assert abs(loss0 - loss1) <= 1e-12 * abs(loss0)
+    assert torch.equal(g0, g1)
