@@ -561,6 +561,93 @@ def run_fwi(args):
                                    "algorithmic_bytes_per_point_step": 64}}), flush=True)
 
 
+def tti_flops_per_point(R):
+    """Floating-point operations of one TTI point update (an FMA counts as
+    two): per field the six derivatives, 18 R^2 + 18 R + 3 (R rows of R
+    first differences for each of the three cross terms, three R-term
+    second derivatives); then H_z of both fields, H_0 of p, the coupling and
+    the two damped leapfrog updates, 55 in all."""
+    return 2 * (18 * R * R + 18 * R + 3) + 55
+
+
+def fp32_peak_tflops():
+    """FP32 peak of one GB300 from its unit counts and clock: 152 SMs x 128
+    FP32 lanes x 2 flops per FMA x 2.07 GHz (the maximum SM clock)."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_tti(args):
+    """The paper's single-GPU TTI grid (896^3 + 40-cell layer, SO 8), a
+    100-step forward run per bench step; Gpts/s over the padded grid and the
+    FP32 roofline of the step kernel."""
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    from paper_2312_13094_gb300 import workloads as wl
+    n = args.n if args.n != 512 else 896
+    nt = args.nt if args.nt != 1000 else 100
+    w = wl.tti_896(n=n, nt=nt)
+    if args.space_order != 8:
+        w["space_order"] = args.space_order
+    R = w["space_order"] // 2
+    npts = int(np.prod(_padded(w)))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = fd.TtiGrid.from_workload(w, stream=stream.cuda_stream)
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+               for a in (w["v"], w["eps"], w["delta"], w["theta"], w["phi"])]
+        g.set_model(*dev)
+        del dev
+        wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+        rec = torch.zeros((nt, len(w["rec"])), device="cuda")
+
+        def one():
+            fd.check(g.forward(w["src"], wav, w["rec"], rec), "fd_tti_forward")
+
+        for _ in range(args.warmup):
+            one()
+        torch.cuda.synchronize()
+        g.set_profiling(True)
+        launches0 = fd.fd_launch_count()
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms = _device_ms(one, stream, args.steps)
+        clk = clocks.stop()
+        launches = fd.fd_launch_count() - launches0
+        info = g.info()
+        g.close()
+    step_ms = info["step_ms"] / max(1, info["steps_timed"])
+    flops = tti_flops_per_point(R) * npts
+    achieved = flops / (step_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    line = {"metric": "Gpts/s", "value": npts * nt / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "grid_padded": _padded(w),
+                       "space_order": w["space_order"], "nt": nt, "nbl": w["nbl"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_kind": "derived: 152 SMs x 128 FP32 "
+                         "lanes x 2 x 2.07 GHz", "flops_per_point": tti_flops_per_point(R),
+                         "kernel": "k_tti_step (avg over the timed step intervals)",
+                         "avg_step_ms": step_ms},
+            "clocks": clk, "gpu_launches": int(launches),
+            "paper_context": {"value": 8.5, "unit": "Gpts/s",
+                              "what": "TTI SO 8, 1x A100-80, 896^3 + ABC (Devito OpenACC)"}}
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import tti as otti
+        wc = wl.tti_workload(n=(88, 88, 88), so=w["space_order"], nbl=4, nt=6, seed=12)
+        og = oracle.Grid(n=wc["n"], h=wc["h"], dt=wc["dt"], R=R, nbl=wc["nbl"])
+        t0 = time.perf_counter()
+        otti.forward(og, wc["v"], wc["eps"], wc["delta"], wc["theta"], wc["phi"], wc["nt"],
+                     wc["src"], wc["wavelet"], wc["rec"])
+        el = time.perf_counter() - t0
+        cpts = int(np.prod(og.padded_shape)) * wc["nt"]
+        line["cpu_baseline"] = {"value": cpts / el / 1e9, "unit": "Gpts/s", "cores": 1,
+                                "kind": "oracle", "sample": f"6 steps of a 96^3 padded TTI grid "
+                                f"(numpy, {el:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Learned per-cell SO 8 weights on the coarse grid vs the plain SO 16
     fine solve: train on fine-run samples of `--train-models` models, then
@@ -623,7 +710,8 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "adjoint", "batched", "learned", "decomposed", "fwi"])
+                    choices=["headline", "adjoint", "batched", "learned", "decomposed", "fwi",
+                             "tti"])
     ap.add_argument("--slabs", type=lambda t: [int(x) for x in t.split(",")], default=[2, 4, 8],
                     help="decomposed workload: slab counts to time")
     ap.add_argument("--train-models", type=int, default=200)
@@ -652,7 +740,7 @@ def main():
         import torch
         torch.cuda.set_device(local)
         {"adjoint": run_adjoint, "batched": run_batched, "learned": run_learned,
-         "decomposed": run_decomposed, "fwi": run_fwi}[args.workload](args)
+         "decomposed": run_decomposed, "fwi": run_fwi, "tti": run_tti}[args.workload](args)
         return
     from paper_2312_13094_gb300 import workloads as wl
     w = wl.acoustic_512(n=args.n, nt=args.nt)

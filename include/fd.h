@@ -359,6 +359,52 @@ fd_status fd_forward_noalloc(const fd_grid_desc* desc, const float* model, int32
                              const fd_points* src, const float* wavelet,
                              const fd_points* rec, float* rec_out);
 
+/* ---- Anisotropic acoustic (TTI) propagation -------------------------------
+ * Sec. IV-B ("Anisotropic acoustic") and App. A (Eq. rot): two fields p, q
+ * coupled through a rotated anisotropic Laplacian (the pseudo-acoustic system
+ * of Zhang et al. 2011, the formulation the paper cites):
+ *     m p_tt + eta p_t = (1+2 eps) H_0 p + sqrt(1+2 delta) H_z q + s,
+ *     m q_tt + eta q_t = sqrt(1+2 delta) H_0 p + H_z q + s,
+ * H_z u = sum_ab n_a n_b D_ab u with the symmetry axis
+ * n = (sin(theta) cos(phi), sin(theta) sin(phi), cos(theta)) (theta the tilt,
+ * phi the azimuth, per cell; Eq. rot's xbar = (cos t cos p, cos t sin p,
+ * -sin t) and ybar = n x xbar complete the rotated frame), H_0 = Laplacian
+ * - H_z, D_aa the centred order-2R second-derivative weights and D_ab (a != b)
+ * the product of the centred order-2R first-derivative weights along a and
+ * b (at space order 16 the paper's 769-point TTI stencil).  Leapfrog in time
+ * with the damping layer, zero ghost, source scaling and trilinear points of
+ * the isotropic path; the layer strength uses v_max sqrt(1+2 eps_max); the
+ * source enters p and q, receivers record I(p^n).  The grid descriptor,
+ * units, memory rules and error codes are those of fd_grid; the library owns
+ * six model fields and two wavefields of each of p and q. */
+typedef struct fd_tti_s* fd_tti;
+fd_status fd_tti_create(const fd_grid_desc* desc, fd_tti* out);
+fd_status fd_tti_destroy(fd_tti grid);
+/* Physical nz*ny*nx arrays (host or device): vp [km/s], Thomsen epsilon and
+ * delta, tilt theta and azimuth phi [rad]; padded into the layer by edge
+ * replication; resets the wavefields.  Errors: FD_ERR_ARG (vp not positive,
+ * 1+2 eps or 1+2 delta not positive, a value not finite), FD_ERR_UNSTABLE
+ * (v_max sqrt(1+2 eps_max) dt / h above the isotropic limit of the space
+ * order; strongly tilted media may need a larger margin). */
+fd_status fd_tti_set_model(fd_tti grid, const float* vp, const float* epsilon,
+                           const float* delta, const float* theta, const float* phi);
+/* desc.nt steps from rest; wavelet [nt][src->n], rec_out [nt][rec->n] = I(p^n). */
+fd_status fd_tti_forward(fd_tti grid, const fd_points* src, const float* wavelet,
+                         const fd_points* rec, float* rec_out);
+/* Continues from the current state for nsteps steps (wavelet rows
+ * n0..n0+nsteps-1; rec_out rows 0..nsteps-1); pointers may be NULL. */
+fd_status fd_tti_propagate(fd_tti grid, int32_t n0, int32_t nsteps, const fd_points* src,
+                           const float* wavelet, const fd_points* rec, float* rec_out);
+/* Replace / read the state (p^{n-1}, p^n, q^{n-1}, q^n) as padded
+ * (nz+2nbl)(ny+2nbl)(nx+2nbl) arrays; any pointer may be NULL. */
+fd_status fd_tti_set_state(fd_tti grid, const float* p_prev, const float* p,
+                           const float* q_prev, const float* q);
+fd_status fd_tti_get_state(fd_tti grid, float* p_prev, float* p, float* q_prev, float* q);
+/* Device time of the steps of later runs (reset when enabled), reported by
+ * fd_tti_get_info in step_ms / steps_timed with the grid's extents. */
+fd_status fd_tti_set_profiling(fd_tti grid, int32_t enabled);
+fd_status fd_tti_get_info(fd_tti grid, fd_grid_info* info);
+
 /* Diagnostics. */
 fd_status fd_get_info(fd_grid grid, fd_grid_info* info);
 /* When enabled, fd_forward / fd_propagate / fd_batch_forward record CUDA

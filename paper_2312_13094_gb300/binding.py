@@ -101,6 +101,15 @@ _SIGS = {
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
     "fd_forward_noalloc": (_S, [ctypes.POINTER(fd_grid_desc), _P, ctypes.c_int32, _PTS, _P,
                                 _PTS, _P]),
+    "fd_tti_create": (_S, [ctypes.POINTER(fd_grid_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "fd_tti_destroy": (_S, [_G]),
+    "fd_tti_set_model": (_S, [_G, _P, _P, _P, _P, _P]),
+    "fd_tti_forward": (_S, [_G, _PTS, _P, _PTS, _P]),
+    "fd_tti_propagate": (_S, [_G, ctypes.c_int32, ctypes.c_int32, _PTS, _P, _PTS, _P]),
+    "fd_tti_set_state": (_S, [_G, _P, _P, _P, _P]),
+    "fd_tti_get_state": (_S, [_G, _P, _P, _P, _P]),
+    "fd_tti_set_profiling": (_S, [_G, ctypes.c_int32]),
+    "fd_tti_get_info": (_S, [_G, ctypes.POINTER(fd_grid_info)]),
     "fd_set_tile": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_decomposition": (_S, [_G, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_schedule": (_S, [_G, ctypes.c_int32]),
@@ -269,6 +278,81 @@ class Grid:
         s, r = Points(src), Points(rec)
         return fd_backward(self.handle, s.ref(), _ptr(wavelet), r.ref(), _ptr(grad_rec),
                            n_checkpoints, _ptr(grad_out))
+
+
+class TtiGrid:
+    """Owns one fd_tti handle (anisotropic acoustic propagation)."""
+
+    def __init__(self, n, h, space_order, nbl, dt, nt, device=0, stream=None):
+        self.desc = fd_grid_desc(int(n[0]), int(n[1]), int(n[2]), float(h), int(space_order),
+                                 int(nbl), float(dt), int(nt), int(device),
+                                 ctypes.c_void_p(stream) if stream else None)
+        self.n = tuple(int(x) for x in n)
+        self.nt = int(nt)
+        handle = ctypes.c_void_p()
+        check(fd_tti_create(ctypes.byref(self.desc), ctypes.byref(handle)), "fd_tti_create")
+        self.handle = handle
+
+    @classmethod
+    def from_workload(cls, w, device=0, stream=None, nt=None):
+        return cls(w["n"], w["h"], w["space_order"], w["nbl"], w["dt"],
+                   w["nt"] if nt is None else nt, device, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fd_tti_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def phys_shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def info(self):
+        i = fd_grid_info()
+        check(fd_tti_get_info(self.handle, ctypes.byref(i)), "fd_tti_get_info")
+        return {k: getattr(i, k) for k, _ in fd_grid_info._fields_}
+
+    @property
+    def padded_shape(self):
+        i = self.info()
+        return (i["nz_pad"], i["ny_pad"], i["nx_pad"])
+
+    def set_model(self, vp, epsilon, delta, theta, phi):
+        check(fd_tti_set_model(self.handle, _ptr(vp), _ptr(epsilon), _ptr(delta), _ptr(theta),
+                               _ptr(phi)), "fd_tti_set_model")
+
+    def set_profiling(self, on=True):
+        check(fd_tti_set_profiling(self.handle, int(on)), "fd_tti_set_profiling")
+
+    def forward(self, src, wavelet, rec, rec_out):
+        s, r = Points(src), Points(rec)
+        return fd_tti_forward(self.handle, s.ref(), _ptr(wavelet), r.ref(), _ptr(rec_out))
+
+    def propagate(self, n0, nsteps, src=None, wavelet=None, rec=None, rec_out=None):
+        s = Points(src) if src is not None else None
+        r = Points(rec) if rec is not None else None
+        return fd_tti_propagate(self.handle, n0, nsteps, s.ref() if s else None, _ptr(wavelet),
+                                r.ref() if r else None, _ptr(rec_out))
+
+    def set_state(self, p_prev=None, p=None, q_prev=None, q=None):
+        check(fd_tti_set_state(self.handle, _ptr(p_prev), _ptr(p), _ptr(q_prev), _ptr(q)),
+              "fd_tti_set_state")
+
+    def get_state(self, p_prev=None, p=None, q_prev=None, q=None):
+        check(fd_tti_get_state(self.handle, _ptr(p_prev), _ptr(p), _ptr(q_prev), _ptr(q)),
+              "fd_tti_get_state")
 
 
 def descent_step(m, grad, step, m_min, m_max, stream=None):

@@ -215,3 +215,58 @@ def cfl_dt(h: float, vmax: float, courant: float = 0.4) -> float:
 
 __all__ = [name for name in globals() if not name.startswith("_")
            and name not in ("annotations", "math", "np")]
+
+
+def tti_model(n, h: float, seed: int, vmin: float = 1.5, vmax: float = 3.5):
+    """Smooth anisotropic (TTI) medium on an n = (nx, ny, nz) grid, physical
+    float32 arrays [nz][ny][nx]: a layered vp (3-6 layers, tanh interfaces),
+    Thomsen eps in [0.05, 0.2] with delta = eps / 2, tilt theta in
+    [0, 0.6] rad and azimuth phi in [0, 1.2] rad, each a product of seeded
+    low-wavenumber sines along the three axes (cheap to build at any size)."""
+    nx, ny, nz = n
+    u = uniform(seed, 32)
+    nl = 3 + int(u[0] * 4)
+    depth = (nz - 1) * h
+    zi = np.sort(u[1:nl] * depth)
+    vel = np.sort(vmin + (vmax - vmin) * u[8:8 + nl])
+    vz = smooth_layers(n, h, zi, vel).astype(np.float32)
+
+    def field(k):
+        ax = [np.sin(2 * np.pi * (0.5 + u[16 + 3 * k + a]) * np.arange(m) / max(m - 1, 1)
+                     + 6.28 * u[16 + 3 * k + a] + 1.0).astype(np.float32)
+              for a, m in enumerate((nx, ny, nz))]
+        return 0.5 + 0.5 * (ax[2][:, None, None] * ax[1][None, :, None] * ax[0][None, None, :])
+
+    shape = (nz, ny, nx)
+    v = np.broadcast_to(vz[:, None, None], shape).astype(np.float32)
+    eps = (0.05 + 0.15 * field(0)).astype(np.float32)
+    delta = (0.5 * eps).astype(np.float32)
+    theta = (0.6 * field(1)).astype(np.float32)
+    phi = (1.2 * field(2)).astype(np.float32)
+    return v, eps, delta, theta, phi
+
+
+def tti_workload(n=(40, 36, 32), so: int = 8, nbl: int = 6, nt: int = 60, seed: int = 11,
+                 courant: float = 0.35, f_hz: float = 15.0, name: str | None = None):
+    """TTI modelling: tti_model medium, dt from the fastest speed
+    v sqrt(1+2 eps), Ricker at the centre, a line of receivers at z = 2.5 h."""
+    h = 10.0
+    v, eps, delta, theta, phi = tti_model(n, h, seed)
+    vfast = float(np.max(v[:, :1, :1] * np.sqrt(1.0 + 2.0 * eps.max())))
+    dt = courant * h / vfast
+    ext = [(d - 1) * h for d in n]
+    src = np.array([[0.5 * ext[0], 0.5 * ext[1], 0.5 * ext[2]]])
+    nrec = min(n[0], 128)
+    rec = np.stack([np.linspace(0.0, ext[0], nrec), np.full(nrec, 0.5 * ext[1]),
+                    np.full(nrec, min(2.5 * h, ext[2]))], axis=1)
+    wav = ricker(nt, dt, f_hz).reshape(nt, 1)
+    return dict(name=name or f"tti {n[0]}x{n[1]}x{n[2]} SO{so} h10 {nt} steps", n=tuple(n), h=h,
+                space_order=so, nbl=nbl, dt=dt, nt=nt, v=v, eps=eps, delta=delta, theta=theta,
+                phi=phi, src=src, rec=rec, wavelet=wav)
+
+
+def tti_896(n: int = 896, nt: int = 100):
+    """The paper's single-GPU TTI grid (Sec. IV-C: 896^3 with a 40-cell
+    absorbing layer, SO 8), 15 Hz Ricker at the centre."""
+    return tti_workload(n=(n, n, n), so=8, nbl=40, nt=nt, seed=12,
+                        name=f"tti {n}^3 SO8 h10 {nt} steps")
