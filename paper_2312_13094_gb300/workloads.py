@@ -20,6 +20,8 @@ source; no dataset is involved):
   * ``batched_shots``    32 windows 128^3..320^3, SO 8, 600 steps
   * ``adjoint_256``      256^3, SO 8, 500 steps, Gaussian anomaly
   * ``learned_pair``     fine 512^3 h 10 SO 16 / coarse 256^3 h 20 SO 8
+  * ``tti_workload``     smooth TTI media (layered vp, eps, delta, tilt and
+                         azimuth), ``tti_896`` the paper's 896^3 SO 8 grid
 """
 from __future__ import annotations
 
