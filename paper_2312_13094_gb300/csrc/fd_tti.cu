@@ -22,8 +22,9 @@
 // derivative, cross terms included, reads shared memory.  Up to space order 8
 // (k_tti_cire) the first x and y differences of each plane are computed once
 // when it enters and kept in rings of their own, so each cross derivative
-// costs 2R shared loads, and each new plane is read into registers one plane
-// ahead, so that its global loads overlap the compute of the plane before;
+// costs 2R shared loads, and each new plane (and the update's per-point
+// model values) is read into registers one plane ahead, so that its global
+// loads overlap the compute of the plane before;
 // the wider stencils (k_tti_step), whose extra rings would not fit, form the
 // cross derivatives as first differences of first differences directly from
 // the u ring, 4R^2 loads each.  The model enters through six per-cell fields
@@ -408,9 +409,25 @@ __global__ void __launch_bounds__(kBX* kBY) k_tti_cire(const __grid_constant__ T
   const int cx = (ty + R) * kBX + tx;     // in a dx plane
   const int dxy = depth(gx, a.nbl, a.nx) * depth(gx, a.nbl, a.nx) +
                   depth(gy, a.nbl, a.ny) * depth(gy, a.nbl, a.ny);
+  // the update's eight values at the thread's point (six model fields and
+  // the previous p and q), read one plane ahead as well; a plane's previous
+  // p and q are only written by the thread that reads them, after the read
+  float pv[8] = {}, pv_next[8] = {};
+  auto fetch_point = [&](int z, float* out) {
+    if (!inside) return;
+    const size_t o = static_cast<size_t>(z) * plane + static_cast<size_t>(gy) * a.pitch + gx;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) out[f] = a.coef[f * a.ncell + o];
+    out[6] = a.pn[o];
+    out[7] = a.qn[o];
+  };
+  fetch_point(z0, pv);
   for (int k = z0; k < z1; ++k) {
     enter(k + R);
-    if (k + 1 < z1) fetch(k + R + 1);  // in flight during this plane's compute
+    if (k + 1 < z1) {  // in flight during this plane's compute
+      fetch(k + R + 1);
+      fetch_point(k + 1, pv_next);
+    }
     if (inside) {
       const int s0 = slot(k);
       float D[2][6];
@@ -441,12 +458,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_tti_cire(const __grid_constant__ T
         D[f][5] = yz;
       }
       const size_t o = static_cast<size_t>(k) * plane + static_cast<size_t>(gy) * a.pitch + gx;
-      const float A = a.coef[o];
-      const float e2 = a.coef[a.ncell + o];
-      const float dl = a.coef[2 * a.ncell + o];
-      const float nx = a.coef[3 * a.ncell + o];
-      const float ny = a.coef[4 * a.ncell + o];
-      const float nz = a.coef[5 * a.ncell + o];
+      const float A = pv[0], e2 = pv[1], dl = pv[2], nx = pv[3], ny = pv[4], nz = pv[5];
       const float wxx = nx * nx, wyy = ny * ny, wzz = nz * nz;
       const float wxy = 2.f * nx * ny, wxz = 2.f * nx * nz, wyz = 2.f * ny * nz;
       const float* dp = D[0];
@@ -462,11 +474,13 @@ __global__ void __launch_bounds__(kBX* kBY) k_tti_cire(const __grid_constant__ T
       const int dz = depth(k, a.nbl, a.nz);
       const float b = a.bscale * static_cast<float>(dxy + dz * dz);
       const float pc = ru[0][s0 * PU + cu], qc = ru[1][s0 * PU + cu];
-      const float pm = a.pn[o], qm = a.qn[o];
+      const float pm = pv[6], qm = pv[7];
       a.pn[o] = (2.f * pc - (1.f - b) * pm + A * rp) / (1.f + b);
       a.qn[o] = (2.f * qc - (1.f - b) * qm + A * rq) / (1.f + b);
     }
     __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 8; ++f) pv[f] = pv_next[f];
   }
 }
 
