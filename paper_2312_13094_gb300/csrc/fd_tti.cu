@@ -735,7 +735,7 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
                         t->stream);
     if (e) return cuda_fail(e, "finite check");
     if (bad) return fail(FD_ERR_NONFINITE, "%d receiver samples are NaN or Inf", bad);
-    if (drec != rec_out) {
+    if (drec != rec_out && nsteps > 0) {
       e = cudaMemcpyAsync(rec_out, drec, size_t(nsteps) * nrec * 4, cudaMemcpyDeviceToHost,
                           t->stream);
       if (e) return cuda_fail(e, "device to host copy");
@@ -845,6 +845,16 @@ fd_status fd_tti_set_model(fd_tti t, const float* vp, const float* epsilon, cons
     fd_status st = stage(t, t->stage_in, in[f], np, size_t(f) * np, &dev[f]);
     if (st) return st;
   }
+  // the staging copy of host arrays is only needed inside this call: freed
+  // on every return, after the work that reads it has finished
+  struct Release {
+    DevBuf& b;
+    cudaStream_t s;
+    ~Release() {
+      if (b.p) cudaStreamSynchronize(s);
+      b.release();
+    }
+  } release_staging{t->stage_in, t->stream};
   unsigned int h[2] = {0, 0};
   unsigned int* s = static_cast<unsigned int*>(t->scratch.p);
   e = cudaMemsetAsync(s, 0, 8, t->stream);
