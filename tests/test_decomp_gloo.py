@@ -1,6 +1,8 @@
 """Domain decomposition along z over CPU ranks (gloo): each rank steps its own
 slab of the padded grid with the FP64 reference step after an R-plane halo
-exchange; the gathered result equals the undecomposed run bit for bit."""
+exchange; the gathered result equals the undecomposed run bit for bit.  A
+rank that leaves before an exchange is reported to its neighbour as an error
+within the process group's timeout (failure made on the host)."""
 import socket
 
 import numpy as np
@@ -89,3 +91,49 @@ def test_decomposed_run_over_gloo_ranks_equals_the_undecomposed_run(world, R):
     import torch.multiprocessing as mp
     oracle.build()
     mp.spawn(_rank_main, args=(world, _free_port(), R, 6), nprocs=world, join=True)
+
+
+def _dead_rank_main(rank, world, port, q):
+    """Rank 1 leaves before the exchange; rank 0 must get an error from its
+    halo exchange within the process group's short timeout, not hang."""
+    import datetime
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}",
+                            world_size=world, rank=rank,
+                            timeout=datetime.timedelta(seconds=4))
+    if rank == 1:
+        q.put((1, "left"))
+        return  # never joins the exchange, never tears down the group
+    ux = torch.zeros((6 + 2 * 2, 5, 5), dtype=torch.float64)
+    try:
+        decomp.exchange_halos(ux, 2, dist, rank, world)
+        q.put((0, "no error"))
+    except Exception as e:  # the missing neighbour surfaces as an error
+        q.put((0, f"error: {type(e).__name__}"))
+
+
+def test_a_rank_that_leaves_is_detected_by_its_neighbour():
+    pytest.importorskip("torch")
+    import multiprocessing as mpl
+    ctx = mpl.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dead_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = {}
+    import queue
+    try:
+        for _ in range(2):
+            r, msg = q.get(timeout=90)
+            got[r] = msg
+    except queue.Empty:
+        pass
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert got.get(1) == "left"
+    assert got.get(0, "").startswith("error"), got
