@@ -1,7 +1,8 @@
 """Pins of the FP64 TTI oracle (oracle/tti.py) against closed forms and
 special cases: the first-derivative weights (exact moment conditions and
 textbook values), the rotated frame of Eq. rot, the discrete derivative
-symbols on a periodic plane wave, the reduction to the isotropic oracle when
+symbols on a periodic plane wave, brute-force stencil sums with the zero
+ghost on a tiny grid, the reduction to the isotropic oracle when
 eps = delta = 0 (any tilt), and plane waves of the coupled system that follow
 its 2 x 2 discrete dispersion relation exactly."""
 import math
@@ -166,3 +167,45 @@ def test_source_reaches_both_fields_and_receivers_read_p():
     w = [oracle.point_weights(g, r) for r in rec]
     last = np.array([np.dot(wt, out["p_prev"].reshape(-1)[i]) for i, wt in w])
     np.testing.assert_allclose(out["rec"][-1], last, rtol=1e-12, atol=1e-300)
+
+
+def test_derivatives_match_brute_force_sums_with_the_zero_ghost():
+    """Every D_ab of a random field on a tiny non-periodic grid equals the
+    explicit double sum over the stencil points, with values beyond the grid
+    taken as zero (the read-only ghost), evaluated point by point."""
+    R = 2
+    g = oracle.Grid(n=(6, 5, 4), h=2.0, dt=1.0, R=R)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(g.padded_shape)
+    D = tti.second_derivatives(g, u)
+    c = oracle.fd_coefficients(R)
+    d = tti.fd1_coefficients(R)
+    Nz, Ny, Nx = u.shape
+
+    def val(z, y, x):
+        return u[z, y, x] if 0 <= z < Nz and 0 <= y < Ny and 0 <= x < Nx else 0.0
+
+    ax = {"x": 2, "y": 1, "z": 0}
+    for (a, b), got in D.items():
+        for z in range(Nz):
+            for y in range(Ny):
+                for x in range(Nx):
+                    p = [z, y, x]
+                    if a == b:
+                        acc = c[0] * val(*p)
+                        for j in range(1, R + 1):
+                            for s in (1, -1):
+                                q = list(p)
+                                q[ax[a]] += s * j
+                                acc += c[j] * val(*q)
+                    else:
+                        acc = 0.0
+                        for i in range(-R, R + 1):
+                            for j in range(-R, R + 1):
+                                if i == 0 or j == 0:
+                                    continue
+                                q = list(p)
+                                q[ax[a]] += i
+                                q[ax[b]] += j
+                                acc += np.sign(i) * d[abs(i)] * np.sign(j) * d[abs(j)] * val(*q)
+                    assert abs(got[z, y, x] - acc / g.h ** 2) <= 1e-12 * (1 + abs(acc))
