@@ -83,6 +83,8 @@ def _load():
         lib.or_adjoint_gradient.restype = ctypes.c_int32
         lib.or_step_slab.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_int64, _D]
         lib.or_step_slab.restype = ctypes.c_int32
+        lib.or_step_block.argtypes = [G, _D, _D, _D, _D, _D, _I64, _D]
+        lib.or_step_block.restype = ctypes.c_int32
         lib.or_step_points.argtypes = [G, _D, ctypes.c_double, _D, _D, _D,
                                        ctypes.c_int64, _I64, _D]
         _lib = lib
@@ -210,6 +212,26 @@ def step_slab(g: Grid, m_pad_s, b_s, u_prev_s, u_cur_x, coef=None):
                              _p(u_prev_s), _p(_f64(u_cur_x)), nzs, _p(out))
     if r != 0:
         raise ValueError("slab steps need a 3-D, non-periodic grid")
+    return out
+
+
+def step_block(g: Grid, m_pad_b, b_b, u_prev_b, u_cur_x, coef=None):
+    """One source-free step of the owned box of a block of a Cartesian
+    decomposition: ``u_cur_x`` holds the box with R ghost layers on every
+    side; the other arrays cover the box ([nz][ny][nx])."""
+    coef = fd_coefficients(g.R) if coef is None else _f64(coef)
+    u_prev_b = _f64(u_prev_b)
+    nz, ny, nx = u_prev_b.shape
+    R = g.R
+    assert u_cur_x.shape == (nz + 2 * R, ny + 2 * R, nx + 2 * R)
+    nb = np.array([nx, ny, nz], dtype=np.int64)
+    out = np.zeros(u_prev_b.shape)
+    gc = g.c()
+    r = _load().or_step_block(ctypes.byref(gc), _p(_f64(m_pad_b)), _p(_f64(b_b)), _p(coef),
+                              _p(u_prev_b), _p(_f64(u_cur_x)), nb.ctypes.data_as(_I64),
+                              _p(out))
+    if r != 0:
+        raise ValueError("block steps need a 3-D, non-periodic grid")
     return out
 
 

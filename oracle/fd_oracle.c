@@ -288,6 +288,47 @@ int32_t or_step_slab(const or_grid* g, const double* m_pad_s, const double* b_s,
   return 0;
 }
 
+/*
+ * The same step on a block of a Cartesian domain decomposition (Sec. III: a
+ * topology of px x py x pz ranks, each owning a box of the padded grid and
+ * reading an R-wide halo of u^n from its neighbours).  The owned box has
+ * nb[0] x nb[1] x nb[2] points (x fastest); u_cur_x holds it with R ghost
+ * layers on every side ([nb2+2R][nb1+2R][nb0+2R], zero where the ghost lies
+ * beyond the global grid); m_pad_b, b_b, u_prev_b and u_next_b cover the
+ * owned box.  Sources are not handled here.  Each point is summed in the
+ * order of or_laplacian and updated as in or_step, so a decomposed run
+ * reproduces the undecomposed one bit for bit.  Returns 0, or -1 for a grid
+ * that is not 3-D and non-periodic.
+ */
+int32_t or_step_block(const or_grid* g, const double* m_pad_b, const double* b_b,
+                      const double* coef, const double* u_prev_b, const double* u_cur_x,
+                      const int64_t* nb, double* u_next_b) {
+  if (g->dims != 3 || g->periodic) return -1;
+  const int R = g->R;
+  const double ih2 = 1.0 / (g->h * g->h);
+  const double dt2 = g->dt * g->dt;
+  const int64_t X0 = nb[0] + 2 * R, X1 = nb[1] + 2 * R;
+  const int64_t stride[3] = {1, X0, X0 * X1};
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int64_t k = 0; k < nb[2]; ++k)
+    for (int64_t j = 0; j < nb[1]; ++j)
+      for (int64_t i = 0; i < nb[0]; ++i) {
+        const int64_t ox = (i + R) + X0 * ((j + R) + X1 * (k + R));
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          acc += coef[0] * u_cur_x[ox];
+          for (int r = 1; r <= R; ++r)
+            acc += coef[r] * (u_cur_x[ox + r * stride[a]] + u_cur_x[ox - r * stride[a]]);
+        }
+        const double L = acc * ih2;
+        const int64_t idx = i + nb[0] * (j + nb[1] * k);
+        const double e = dt2 / m_pad_b[idx] * L;
+        u_next_b[idx] =
+            (2.0 * u_cur_x[ox] - (1.0 - b_b[idx]) * u_prev_b[idx] + e) / (1.0 + b_b[idx]);
+      }
+  return 0;
+}
+
 /* Forward-Euler heat step u_next = u + dt * L u (Sec. II, Listing 1). */
 void or_heat_step(const or_grid* g, const double* u, double* scratch_L,
                   double* u_next) {

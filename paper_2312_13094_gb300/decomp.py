@@ -1,16 +1,21 @@
-"""Domain decomposition of one grid along z (the paper's basic mode, Sec. III:
-each subdomain exchanges an R-deep halo with its neighbours before every step).
+"""Domain decomposition of one grid over ranks (the paper's Sec. III: each
+subdomain exchanges an R-deep halo with its neighbours before every step).
 
-This module holds only the data movement of that scheme: which padded z planes
-a rank owns, and the halo exchange that fills the R ghost planes on either
-side of a rank's slab with its neighbours' edge planes.  The step itself is
-whatever the caller computes on the slab (the FD kernels of libfd.so need a
-slab with ghost planes of their own, which they do not have yet; the CPU tests
-run the exchange between gloo ranks around the FP64 reference step).
+This module holds the data movement of that scheme, not the step itself:
+  * slabs along z: which padded z planes a rank owns (slab_range) and the
+    exchange that fills the R ghost planes on either side (exchange_halos);
+    the device runs the same split inside one GPU (fd_set_decomposition);
+  * a Cartesian topology of px x py x pz ranks (dims_create, Topology) and the
+    paper's basic-mode exchange on it (exchange_halos_3d): one synchronous
+    step per axis, two packed face messages each, later axes carrying the
+    edges and corners.
+The CPU tests run these exchanges between gloo ranks around the FP64
+reference step and compare with the undecomposed run bit for bit.
 
-Layout of a rank's extended array: [R ghost planes | nzs owned planes | R ghost
-planes] along the first axis; ghost planes beyond the global grid stay zero
-(the read-only zero halo of Sec. III).
+Layout of a rank's extended array: its owned points with R ghost layers
+around them (along z only for slabs, along every axis for Cartesian blocks);
+ghost layers beyond the global grid are zero (the read-only zero halo of
+Sec. III).
 """
 from __future__ import annotations
 
@@ -54,3 +59,112 @@ def exchange_halos(u_x, R: int, dist, rank: int, world: int) -> None:
         u_x[0:R].copy_(lo)
     if hi is not None:
         u_x[nzs + R:].copy_(hi)
+
+
+# ---------------------------------------------------------------------------
+# Cartesian topology (Sec. III: the grid is split over an MPI Cartesian
+# topology of px x py x pz ranks, chosen by the library or given by the user
+# as topology=(px, py, pz))
+# ---------------------------------------------------------------------------
+
+def dims_create(world: int, ndims: int = 3) -> tuple:
+    """A balanced split of `world` ranks over `ndims` axes: the prime factors
+    of world dealt largest first to the axis with the fewest ranks so far,
+    returned in non-increasing order (as MPI_Dims_create does); axis order
+    (x, y, z)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    f, n, p = [], world, 2
+    while p * p <= n:
+        while n % p == 0:
+            f.append(p)
+            n //= p
+        p += 1
+    if n > 1:
+        f.append(n)
+    dims = [1] * ndims
+    for q in sorted(f, reverse=True):
+        dims[dims.index(min(dims))] *= q
+    return tuple(sorted(dims, reverse=True))
+
+
+class Topology:
+    """Rank layout of a Cartesian decomposition: dims = (px, py, pz), rank
+    = (cz * py + cy) * px + cx (x fastest); each axis split into balanced
+    contiguous ranges of the padded grid (slab_range per axis)."""
+
+    def __init__(self, dims, shape_xyz):
+        self.dims = tuple(int(d) for d in dims)
+        self.shape = tuple(int(s) for s in shape_xyz)
+        if len(self.dims) != 3 or min(self.dims) < 1:
+            raise ValueError(f"bad topology {dims}")
+        for d, s in zip(self.dims, self.shape):
+            if d > s:
+                raise ValueError(f"cannot split {s} points over {d} ranks")
+        self.world = self.dims[0] * self.dims[1] * self.dims[2]
+
+    def coords(self, rank: int) -> tuple:
+        px, py, _ = self.dims
+        if not 0 <= rank < self.world:
+            raise ValueError(f"rank {rank} outside a world of {self.world}")
+        return rank % px, (rank // px) % py, rank // (px * py)
+
+    def rank_of(self, coords) -> int | None:
+        """Rank at coords, or None outside the topology (the grid's edge)."""
+        if any(c < 0 or c >= d for c, d in zip(coords, self.dims)):
+            return None
+        cx, cy, cz = coords
+        return (cz * self.dims[1] + cy) * self.dims[0] + cx
+
+    def box(self, rank: int) -> tuple:
+        """((x0, nx), (y0, ny), (z0, nz)): the padded points a rank owns."""
+        return tuple(slab_range(s, d, c) for s, d, c in zip(self.shape, self.dims,
+                                                              self.coords(rank)))
+
+    def neighbour(self, rank: int, axis: int, step: int) -> int | None:
+        c = list(self.coords(rank))
+        c[axis] += step
+        return self.rank_of(c)
+
+
+def exchange_halos_3d(u_x, R: int, dist, topo: Topology, rank: int) -> None:
+    """Fill the R-wide ghost layers of the extended block `u_x`
+    ([nz + 2R, ny + 2R, nx + 2R] tensor, the owned box in the middle) from the
+    neighbours, in the paper's basic mode: one synchronous step per axis, x,
+    then y, then z, two messages each (six in all).  A step sends the R owned
+    layers next to each face, packed into a contiguous buffer; across the
+    axes already exchanged the face includes their ghost layers, so edges and
+    corners arrive too (what cross-derivative stencils such as TTI's need).
+    Ghost layers beyond the grid are zero.  Every rank must call this."""
+    nz, ny, nx = (s - 2 * R for s in u_x.shape)
+    n = {0: nx, 1: ny, 2: nz}
+    if min(n.values()) < R:
+        raise ValueError("a block needs at least R points along every axis")
+    done = []
+    for axis in (0, 1, 2):  # x, y, z
+        dim = 2 - axis      # tensor dimension of this axis
+        idx = [slice(R, R + n[a]) if a not in done else slice(None) for a in (2, 1, 0)]
+        # idx is in tensor order (z, y, x); the axis itself is set per face
+
+        def face(lo, hi):
+            sl = list(idx)
+            sl[dim] = slice(lo, hi)
+            return tuple(sl)
+
+        reqs, recv = [], []
+        for step, (own, ghost) in ((-1, ((R, 2 * R), (0, R))),
+                                   (1, ((n[axis], n[axis] + R), (n[axis] + R, n[axis] + 2 * R)))):
+            peer = topo.neighbour(rank, axis, step)
+            gsl = face(*ghost)
+            if peer is None:
+                u_x[gsl] = 0
+                continue
+            reqs.append(dist.isend(u_x[face(*own)].contiguous(), peer, tag=10 * axis + (step + 1)))
+            buf = u_x.new_empty(u_x[gsl].shape)
+            reqs.append(dist.irecv(buf, peer, tag=10 * axis + (1 - step)))
+            recv.append((gsl, buf))
+        for r in reqs:
+            r.wait()
+        for gsl, buf in recv:
+            u_x[gsl] = buf
+        done.append(axis)
