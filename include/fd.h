@@ -22,6 +22,15 @@
  * are injected and receivers interpolated with trilinear weights (Sec. III
  * "Sparse data"); s^n = sum_src w q(t_n) / h^3 and rec[n] = I(u^n).
  *
+ * Beyond that step the library has: the adjoint gradient (fd_adjoint_gradient,
+ * fd_backward), many shots per launch (fd_batch_forward), learned stencil
+ * weights (fd_mlp_*, fd_set_learned_*), work schedules and their tuning
+ * (fd_set_tile, fd_set_schedule), a z decomposition into slabs with halo
+ * exchange on the device (fd_set_decomposition, Sec. III), the model update
+ * of an inversion loop (fd_descent_step), the anisotropic TTI system of
+ * Sec. IV-B (fd_tti_*) and a forward run that allocates nothing
+ * (fd_forward_noalloc).
+ *
  * Units: h in metres, dt in milliseconds, velocity in km/s, m in (ms/m)^2.
  *
  * Memory: every float array argument may be HOST or DEVICE memory on the
