@@ -61,6 +61,54 @@ def exchange_halos(u_x, R: int, dist, rank: int, world: int) -> None:
         u_x[nzs + R:].copy_(hi)
 
 
+def halo_begin(u_x, R: int, dist, rank: int, world: int):
+    """Start the slab exchange of exchange_halos without waiting (the paper's
+    "full" mode, Sec. III: the halo travels while the CORE planes, whose
+    stencils stay inside the slab, are computed).  Returns the pending state
+    for halo_end; ghost planes beyond the grid are zeroed at once."""
+    nzs = u_x.shape[0] - 2 * R
+    if nzs < R:
+        raise ValueError(f"a slab of {nzs} planes cannot feed an {R}-plane halo")
+    reqs, recv = [], []
+    if rank > 0:
+        reqs.append(dist.isend(u_x[R:2 * R].contiguous(), rank - 1, tag=1))
+        lo = u_x.new_empty(u_x[0:R].shape)
+        reqs.append(dist.irecv(lo, rank - 1, tag=2))
+        recv.append((slice(0, R), lo))
+    else:
+        u_x[0:R].zero_()
+    if rank + 1 < world:
+        reqs.append(dist.isend(u_x[nzs:nzs + R].contiguous(), rank + 1, tag=2))
+        hi = u_x.new_empty(u_x[nzs + R:].shape)
+        reqs.append(dist.irecv(hi, rank + 1, tag=1))
+        recv.append((slice(nzs + R, nzs + 2 * R), hi))
+    else:
+        u_x[nzs + R:].zero_()
+    return u_x, reqs, recv
+
+
+def halo_end(pending) -> None:
+    """Wait for the messages of halo_begin and place the received ghost
+    planes (the REMAINDER planes can then be computed)."""
+    u_x, reqs, recv = pending
+    for r in reqs:
+        r.wait()
+    for sl, buf in recv:
+        u_x[sl] = buf
+
+
+def core_and_remainder(nzs: int, R: int, rank: int, world: int):
+    """Owned-plane ranges of a slab: the CORE planes, whose stencils read no
+    ghost plane, and the REMAINDER planes beside an inner face (ranges are
+    [a, b) in owned-plane numbering; a slab at the end of the grid has no
+    remainder on that side, since its ghost planes there are zero)."""
+    lo = R if rank > 0 else 0
+    hi = R if rank + 1 < world else 0
+    core = (lo, nzs - hi) if nzs - hi > lo else (0, 0)
+    rem = [r for r in ((0, lo), (nzs - hi, nzs)) if r[1] > r[0]]
+    return core, rem
+
+
 # ---------------------------------------------------------------------------
 # Cartesian topology (Sec. III: the grid is split over an MPI Cartesian
 # topology of px x py x pz ranks, chosen by the library or given by the user

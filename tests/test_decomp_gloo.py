@@ -1,8 +1,10 @@
 """Domain decomposition along z over CPU ranks (gloo): each rank steps its own
 slab of the padded grid with the FP64 reference step after an R-plane halo
-exchange; the gathered result equals the undecomposed run bit for bit.  A
-rank that leaves before an exchange is reported to its neighbour as an error
-within the process group's timeout (failure made on the host)."""
+exchange (basic mode), or steps its CORE planes while the exchange travels
+and its REMAINDER planes after it (full mode); the gathered result equals
+the undecomposed run bit for bit.  A rank that leaves before an exchange is
+reported to its neighbour as an error within the process group's timeout
+(failure made on the host)."""
 import socket
 
 import numpy as np
@@ -137,3 +139,63 @@ def test_a_rank_that_leaves_is_detected_by_its_neighbour():
             p.join()
     assert got.get(1) == "left"
     assert got.get(0, "").startswith("error"), got
+
+
+def _full_mode_main(rank, world, port, R, nt):
+    """The paper's full mode on z slabs: start the exchange, step the CORE
+    planes while it travels, finish it, then step the REMAINDER planes."""
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}",
+                            world_size=world, rank=rank)
+    try:
+        g, m_pad, b, up, uc = _problem(R)
+        z0, nzs = decomp.slab_range(g.padded_shape[0], world, rank)
+        own = slice(z0, z0 + nzs)
+        prev = up[own].copy()
+        ux = torch.full((nzs + 2 * R,) + up.shape[1:], float("nan"), dtype=torch.float64)
+        ux[R:R + nzs] = torch.from_numpy(uc[own])
+        core, rem = decomp.core_and_remainder(nzs, R, rank, world)
+        for _ in range(nt):
+            pend = decomp.halo_begin(ux, R, dist, rank, world)
+            nxt = np.full(prev.shape, np.nan)
+
+            def part(a, b_):
+                # owned planes [a, b_) from extended planes [a, b_ + 2R)
+                return oracle.step_slab(g, m_pad[own][a:b_], b[own][a:b_], prev[a:b_],
+                                        ux.numpy()[a:b_ + 2 * R])
+
+            if core[1] > core[0]:
+                nxt[core[0]:core[1]] = part(*core)  # no ghost plane read yet
+            decomp.halo_end(pend)
+            for a, b_ in rem:
+                nxt[a:b_] = part(a, b_)
+            prev = ux[R:R + nzs].numpy().copy()
+            ux[R:R + nzs] = torch.from_numpy(nxt)
+        parts = [None] * world
+        dist.all_gather_object(parts, (z0, ux[R:R + nzs].numpy().copy()))
+        if rank == 0:
+            got = np.concatenate([p for _, p in sorted(parts, key=lambda t: t[0])])
+            pu, cu = up, uc
+            for _ in range(nt):
+                nu, _ = oracle.step(g, m_pad, b, pu, cu)
+                pu, cu = cu, nu
+            np.testing.assert_array_equal(got, cu)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,R", [(2, 2), (3, 4)])
+def test_full_mode_core_then_remainder_equals_the_undecomposed_run(world, R):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    oracle.build()
+    mp.spawn(_full_mode_main, args=(world, _free_port(), R, 5), nprocs=world, join=True)
+
+
+@pytest.mark.parametrize("nzs,R,rank,world,core,rem", [
+    (10, 2, 0, 1, (0, 10), []), (10, 2, 0, 3, (0, 8), [(8, 10)]),
+    (10, 2, 1, 3, (2, 8), [(0, 2), (8, 10)]), (10, 2, 2, 3, (2, 10), [(0, 2)]),
+    (4, 2, 1, 3, (0, 0), [(0, 2), (2, 4)])])
+def test_core_and_remainder_ranges(nzs, R, rank, world, core, rem):
+    assert decomp.core_and_remainder(nzs, R, rank, world) == (core, rem)
