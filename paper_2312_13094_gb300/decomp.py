@@ -8,7 +8,10 @@ This module holds the data movement of that scheme, not the step itself:
   * a Cartesian topology of px x py x pz ranks (dims_create, Topology) and the
     paper's basic-mode exchange on it (exchange_halos_3d): one synchronous
     step per axis, two packed face messages each, later axes carrying the
-    edges and corners.
+    edges and corners; and its diagonal mode (exchange_halos_diag): one step
+    with up to 26 messages, faces, edges and corners at once;
+  * the full mode on slabs (halo_begin, halo_end, core_and_remainder): the
+    CORE planes are stepped while the exchange travels.
 The CPU tests run these exchanges between gloo ranks around the FP64
 reference step and compare with the undecomposed run bit for bit.
 
@@ -216,3 +219,50 @@ def exchange_halos_3d(u_x, R: int, dist, topo: Topology, rank: int) -> None:
         for gsl, buf in recv:
             u_x[gsl] = buf
         done.append(axis)
+
+
+def exchange_halos_diag(u_x, R: int, dist, topo: Topology, rank: int) -> int:
+    """The paper's diagonal mode on the same blocks: one step in which the
+    block exchanges with all 26 face, edge and corner neighbours at once
+    (each message the R-deep part of the owned box next to that neighbour),
+    instead of three axis steps.  Ghost regions beyond the grid are zero.
+    Returns the number of messages sent."""
+    nz, ny, nx = (s - 2 * R for s in u_x.shape)
+    n = (nx, ny, nz)
+    if min(n) < R:
+        raise ValueError("a block needs at least R points along every axis")
+
+    def rng(axis, d, ghost):
+        if d == 0:
+            return slice(R, R + n[axis])
+        if ghost:
+            return slice(0, R) if d < 0 else slice(n[axis] + R, n[axis] + 2 * R)
+        return slice(R, 2 * R) if d < 0 else slice(n[axis], n[axis] + R)
+
+    def code(off):
+        return (off[0] + 1) + 3 * (off[1] + 1) + 9 * (off[2] + 1)
+
+    cx, cy, cz = topo.coords(rank)
+    reqs, recv, sent = [], [], 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                off = (dx, dy, dz)
+                if off == (0, 0, 0):
+                    continue
+                gsl = (rng(2, dz, True), rng(1, dy, True), rng(0, dx, True))
+                peer = topo.rank_of((cx + dx, cy + dy, cz + dz))
+                if peer is None:
+                    u_x[gsl] = 0
+                    continue
+                osl = (rng(2, dz, False), rng(1, dy, False), rng(0, dx, False))
+                reqs.append(dist.isend(u_x[osl].contiguous(), peer, tag=100 + code(off)))
+                sent += 1
+                buf = u_x.new_empty(u_x[gsl].shape)
+                reqs.append(dist.irecv(buf, peer, tag=100 + code((-dx, -dy, -dz))))
+                recv.append((gsl, buf))
+    for r in reqs:
+        r.wait()
+    for gsl, buf in recv:
+        u_x[gsl] = buf
+    return sent

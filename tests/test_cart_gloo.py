@@ -107,12 +107,24 @@ def _only_box(a, box, R):
     return out
 
 
-def _rank_main(rank, world, port, dims, kind, nt):
+def _rank_main(rank, world, port, dims, kind, nt, mode="basic"):
     import torch
     import torch.distributed as dist
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}",
                             world_size=world, rank=rank)
     try:
+        def exchange(u_x, R, topo):
+            if mode == "diag":
+                sent = decomp.exchange_halos_diag(u_x, R, dist, topo, rank)
+                c = topo.coords(rank)
+                # one message per existing neighbour among the 26 directions
+                want = sum(1 for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                           if (dx, dy, dz) != (0, 0, 0) and
+                           topo.rank_of((c[0] + dx, c[1] + dy, c[2] + dz)) is not None)
+                assert sent == want
+            else:
+                decomp.exchange_halos_3d(u_x, R, dist, topo, rank)
+
         if kind == "acoustic":
             g, m_pad, b, up, uc = _acoustic_problem(2)
             R = g.R
@@ -123,7 +135,7 @@ def _rank_main(rank, world, port, dims, kind, nt):
             prev = up[own].copy()
             ux = torch.from_numpy(_only_box(uc, box, R))
             for _ in range(nt):
-                decomp.exchange_halos_3d(ux, R, dist, topo, rank)
+                exchange(ux, R, topo)
                 nxt = oracle.step_block(g, m_pad[own], b[own], prev, ux.numpy())
                 prev = _own(ux.numpy(), R).copy()
                 ux[R:-R, R:-R, R:-R] = torch.from_numpy(nxt)
@@ -149,8 +161,8 @@ def _rank_main(rank, world, port, dims, kind, nt):
             px = torch.from_numpy(_only_box(st[1], box, R))
             qx = torch.from_numpy(_only_box(st[3], box, R))
             for _ in range(nt):
-                decomp.exchange_halos_3d(px, R, dist, topo, rank)
-                decomp.exchange_halos_3d(qx, R, dist, topo, rank)
+                exchange(px, R, topo)
+                exchange(qx, R, topo)
                 pn, qn = otti.step(g, *coef, bx, p_prev, px.numpy(), q_prev, qx.numpy())
                 p_prev, q_prev = px.numpy().copy(), qx.numpy().copy()
                 px[R:-R, R:-R, R:-R] = torch.from_numpy(_own(pn, R))
@@ -182,11 +194,17 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("dims,kind", [((2, 2, 1), "acoustic"), ((1, 2, 3), "acoustic"),
-                                       ((2, 2, 2), "tti")])
-def test_cartesian_run_over_gloo_ranks_equals_the_undecomposed_run(dims, kind):
+@pytest.mark.parametrize("dims,kind,mode", [((2, 2, 1), "acoustic", "basic"),
+                                            ((1, 2, 3), "acoustic", "basic"),
+                                            ((2, 2, 2), "tti", "basic"),
+                                            ((2, 2, 2), "tti", "diag"),
+                                            ((3, 1, 2), "acoustic", "diag")])
+def test_cartesian_run_over_gloo_ranks_equals_the_undecomposed_run(dims, kind, mode):
+    """Basic mode (three axis steps) and diagonal mode (one step, up to 26
+    messages per rank) both give the undecomposed run's bits."""
     pytest.importorskip("torch")
     import torch.multiprocessing as mp
     oracle.build()
     world = dims[0] * dims[1] * dims[2]
-    mp.spawn(_rank_main, args=(world, _free_port(), dims, kind, 4), nprocs=world, join=True)
+    mp.spawn(_rank_main, args=(world, _free_port(), dims, kind, 4, mode), nprocs=world,
+             join=True)
