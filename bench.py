@@ -664,8 +664,14 @@ def run_learned(args):
     from paper_2312_13094_gb300 import learned as lr
     n, nt = args.n, (args.nt if args.nt != 1000 else 1250)
     if args.params:
-        # evaluate a network trained earlier (FD_MLP_NPARAM floats, .npy)
-        net = lr.Network(np.load(args.params).astype(np.float32))
+        # evaluate a network trained earlier (a checkpoint, or FD_MLP_NPARAM
+        # floats as .npy)
+        if args.params.endswith(".npy"):
+            p = np.load(args.params).astype(np.float32)
+        else:
+            from paper_2312_13094_gb300 import checkpoint
+            p, _ = checkpoint.load(args.params)
+        net = lr.Network(p)
         S = torch.zeros((0, 10))
         l0 = l1 = t_data = t_train = None
     else:
@@ -686,6 +692,11 @@ def run_learned(args):
                        ladder=args.ladder)
     os.makedirs(_out_dir(), exist_ok=True)
     np.save(os.path.join(_out_dir(), "learned_params.npy"), net.params())
+    from paper_2312_13094_gb300 import checkpoint
+    checkpoint.save(os.path.join(_out_dir(), "learned_params.fdck"), net.params(),
+                    {"train_models": args.train_models, "epochs": args.epochs,
+                     "loss_before": l0, "loss_after": l1, "samples": int(S.shape[0]),
+                     "grid": f"fine {n}^3 h10 SO16 / coarse {n // 2}^3 h20 SO8"})
 
     def mean(key):
         return float(np.mean([r[key] for r in rows]))
@@ -726,7 +737,8 @@ def main():
     ap.add_argument("--test-models", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--params", default="",
-                    help="learned workload: evaluate these network parameters (.npy), no training")
+                    help="learned workload: evaluate a trained network (checkpoint or .npy), "
+                         "no training")
     ap.add_argument("--ladder", action="store_true",
                     help="learned workload: also time plain SO 8/16 at h 16 and 12.8 m")
     ap.add_argument("--gpus", type=int, default=1)
