@@ -36,32 +36,10 @@ def exchange_halos(u_x, R: int, dist, rank: int, world: int) -> None:
     """Fill the ghost planes of the extended slab `u_x` ([nzs + 2R, ...]
     tensor) in place: planes [0, R) from rank - 1's last R owned planes,
     planes [nzs + R, nzs + 2R) from rank + 1's first R owned planes; at the
-    ends of the grid they are set to zero.  Every rank must call this with
-    the same R; each slab needs at least R owned planes."""
-    nzs = u_x.shape[0] - 2 * R
-    if nzs < R:
-        raise ValueError(f"a slab of {nzs} planes cannot feed an {R}-plane halo")
-    reqs = []
-    if rank > 0:
-        reqs.append(dist.isend(u_x[R:2 * R].contiguous(), rank - 1, tag=1))
-        lo = u_x.new_empty(u_x[0:R].shape)
-        reqs.append(dist.irecv(lo, rank - 1, tag=2))
-    else:
-        lo = None
-        u_x[0:R].zero_()
-    if rank + 1 < world:
-        reqs.append(dist.isend(u_x[nzs:nzs + R].contiguous(), rank + 1, tag=2))
-        hi = u_x.new_empty(u_x[nzs + R:].shape)
-        reqs.append(dist.irecv(hi, rank + 1, tag=1))
-    else:
-        hi = None
-        u_x[nzs + R:].zero_()
-    for r in reqs:
-        r.wait()
-    if lo is not None:
-        u_x[0:R].copy_(lo)
-    if hi is not None:
-        u_x[nzs + R:].copy_(hi)
+    ends of the grid they are set to zero (the paper's basic mode: the whole
+    exchange before the step).  Every rank must call this with the same R;
+    each slab needs at least R owned planes."""
+    halo_end(halo_begin(u_x, R, dist, rank, world))
 
 
 def halo_begin(u_x, R: int, dist, rank: int, world: int):
