@@ -209,3 +209,46 @@ def test_derivatives_match_brute_force_sums_with_the_zero_ghost():
                                 q[ax[b]] += j
                                 acc += np.sign(i) * d[abs(i)] * np.sign(j) * d[abs(j)] * val(*q)
                     assert abs(got[z, y, x] - acc / g.h ** 2) <= 1e-12 * (1 + abs(acc))
+
+
+def _max_eigen(R, eps, delta, theta, phi, nk=10):
+    """Largest |eigenvalue| (times h^2) of the 2 x 2 symbol matrix of the
+    discrete TTI system over a grid of wavenumbers k h in [0, pi]^3 (the
+    symbol is even in k, so one octant with both signs of two axes)."""
+    c = oracle.fd_coefficients(R)
+    d = tti.fd1_coefficients(R)
+    J = np.arange(1, R + 1)
+    xb, yb, zb = (f.reshape(3) for f in tti.frame(np.array(theta), np.array(phi)))
+    e, dl = 1 + 2 * eps, math.sqrt(1 + 2 * delta)
+    worst = 0.0
+    for kx in np.linspace(0, np.pi, nk):
+        for ky in np.linspace(-np.pi, np.pi, 2 * nk):
+            for kz in np.linspace(-np.pi, np.pi, 2 * nk):
+                k = (kx, ky, kz)
+                S = [2 * np.sum(d[1:] * np.sin(J * ka)) for ka in k]
+                s2 = [c[0] + 2 * np.sum(c[1:] * np.cos(J * ka)) for ka in k]
+                sym = np.array([[s2[a] if a == b else -S[a] * S[b] for b in range(3)]
+                                for a in range(3)])
+                hz, h0 = zb @ sym @ zb, xb @ sym @ xb + yb @ sym @ yb
+                lam = np.linalg.eigvals(np.array([[e * h0, dl * hz], [dl * h0, hz]]))
+                worst = max(worst, float(np.max(np.abs(lam))))
+    return worst
+
+
+@pytest.mark.parametrize("R", [2, 4])
+def test_accepted_tti_models_are_stable_in_the_workload_ranges(R):
+    """Frozen-coefficient (von Neumann) analysis: leapfrog stability needs
+    (dt^2 v^2 / h^2) |lambda| <= 4 for every eigenvalue of the symbol matrix.
+    Over the workloads' ranges (eps <= 0.2, delta = eps / 2, tilt <= 0.6 rad,
+    azimuths 0..1.2 rad), sampled on a wavenumber grid that includes the
+    Nyquist corners, the largest Courant number v sqrt(1+2 eps) dt / h this
+    allows is above the isotropic limit the library checks against, so the
+    check is conservative there; with eps = delta = 0 the bound is exactly the
+    isotropic one."""
+    c = oracle.fd_coefficients(R)
+    iso = -c[0] - 2 * np.sum(c[1:] * (-1.0) ** np.arange(1, R + 1))  # 1-D Nyquist symbol
+    iso_limit = math.sqrt(4.0 / (3.0 * iso))
+    assert abs(math.sqrt(4.0 / _max_eigen(R, 0.0, 0.0, 0.3, 0.5)) - iso_limit) < 1e-9
+    lam = max(_max_eigen(R, 0.2, 0.1, t, p) for t in (0.0, 0.3, 0.6) for p in (0.0, 0.6, 1.2))
+    tti_limit = math.sqrt(4.0 * 1.4 / lam)  # in units of the fast speed v sqrt(1 + 2 eps)
+    assert tti_limit > iso_limit
