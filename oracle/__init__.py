@@ -13,8 +13,9 @@ coefficient network, ``fwi.py`` that of the inversion loop's model update.
 Pinned: coefficients (moment conditions), the heat worked example (Sec. II,
 Listings 1-3), d'Alembert at Courant 1, plane-wave dispersion, energy balance
 with damping, Green's functions, multilinear weights, the adjoint gradient
-(brute-force central differences) and the MLP backward pass (central
-differences).  The absorbing-layer profile strength (gamma_max) is a reading,
+(brute-force central differences), the MLP backward pass (central
+differences) and the sampled step ``step_points`` (equal to the full-grid
+step at every cell of a grid with a layer).  The absorbing-layer profile strength (gamma_max) is a reading,
 checked only by its properties: parity unpinned for that constant.
 """
 from __future__ import annotations

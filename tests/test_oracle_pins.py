@@ -434,3 +434,68 @@ def test_adjoint_is_transpose_of_linearised_modelling():
     lhs = np.sum((jp - jm) / (2 * eps) * r)
     rhs = np.sum(dm * grad)
     assert abs(lhs - rhs) <= 1e-7 * abs(lhs)
+
+
+# --------------------------------------------------------------------------
+# Sampled single step (the checker of the full-size GPU tests) against the
+# full-grid step
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R,n,nbl", [(4, (13, 11, 9), 6), (1, (5, 7, 6), 3), (8, (18, 17, 19), 5),
+                                     (2, (9, 8, 7), 0)])
+def test_step_points_equals_full_step_everywhere(R, n, nbl):
+    """or_step_points restates the damped leapfrog update (layer depth, model
+    lookup by edge replication, zero ghost) for listed cells only.  Evaluated
+    at EVERY padded cell of a small grid with a layer, from a random state on
+    a model that varies along all three axes, it must equal or_step (pinned
+    above by the worked example, d'Alembert, dispersion, energy and Green's
+    functions) to rounding: the two differ only in where h^-2 is applied."""
+    h, dt = 10.0, 1.1
+    g = oracle.Grid(n=n, h=h, dt=dt, R=R, nbl=nbl)
+    shp = g.padded_shape
+    nz, ny, nx = g.phys_shape
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    v = 1.5 + 0.1 * zz + 0.07 * yy + 0.05 * xx + 0.3 * np.sin(xx * yy + zz)
+    m = 1.0 / v ** 2
+    vmax = float(v.max())
+    up = wl.random_state(shp, 41 + R)
+    uc = wl.random_state(shp, 42 + R)
+    ref, _ = oracle.step(g, oracle.pad_model(g, m), oracle.damping(g, vmax), up, uc)
+    idx = np.arange(int(np.prod(shp)), dtype=np.int64)
+    got = oracle.step_points(g, m, vmax, up, uc, idx).reshape(shp)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-15 * scale * (2 * R + 2)
+    # the layer is present and matters: the corner cells are damped
+    if nbl:
+        b = oracle.damping(g, vmax)
+        assert b[0, 0, 0] > 0.05
+        assert abs(got[0, 0, 0] - ref[0, 0, 0]) <= 1e-14 * scale
+        assert abs(got[-1, -1, -1] - ref[-1, -1, -1]) <= 1e-14 * scale
+
+
+def test_step_points_detects_a_wrong_layer_depth():
+    """A planted off-by-one in the layer's far-side depth (as the restated
+    formula could carry) moves the cells of the far faces well outside the
+    rounding bound of the test above: the pin is sensitive to it."""
+    R, n, nbl, h, dt = 4, (13, 11, 9), 6, 10.0, 1.1
+    g = oracle.Grid(n=n, h=h, dt=dt, R=R, nbl=nbl)
+    shp = g.padded_shape
+    m = np.full(g.phys_shape, 1.0 / 2.0 ** 2)
+    up = wl.random_state(shp, 5)
+    uc = wl.random_state(shp, 6)
+    ref, _ = oracle.step(g, oracle.pad_model(g, m), oracle.damping(g, 2.0), up, uc)
+    # the same step with the far-side depth shifted by one cell: b of every
+    # cell from the far face of the physical box outward takes the depth + 1
+    b_bad = oracle.damping(g, 2.0)
+    Nz, Ny, Nx = shp
+    gmax = 3.0 * 2.0 * math.log(1e3) / (2 * nbl * h)
+    for i in range(Nx):
+        d_ok = max(nbl - i, i - (n[0] + nbl - 1), 0) / nbl
+        d_bad = max(nbl - i, i - (n[0] + nbl - 2), 0) / nbl
+        b_bad[:, :, i] += gmax * (d_bad ** 2 - d_ok ** 2) * dt / 2
+    bad, _ = oracle.step(g, oracle.pad_model(g, m), b_bad, up, uc)
+    idx = np.arange(int(np.prod(shp)), dtype=np.int64)
+    got = oracle.step_points(g, m, 2.0, up, uc, idx).reshape(shp)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-15 * scale * 10
+    assert np.abs(got - bad).max() > 1e-4 * scale
