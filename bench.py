@@ -32,8 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALGO_BYTES_PER_POINT = 16  # read u^n, u^{n-1}, A; write u^{n+1}
-_SCHED = {"auto": 0, "shares": 1, "waves": 2}
-_SCHED_NAME = {1: "shares", 2: "waves"}
+_SCHED = {"auto": 0, "shares": 1, "waves": 2, "temporal": 3}
+_SCHED_NAME = {1: "shares", 2: "waves", 3: "temporal"}
+# algorithmic bytes per point of one launch: a single step reads u^n, u^{n-1},
+# A and writes u^{n+1}; a two-step pass (temporal blocking) reads the same
+# three and writes u^{n+1} and u^{n+2}
+_LAUNCH_BYTES = {"single": 16, "temporal": 20}
 
 
 def _peaks():
@@ -162,8 +166,31 @@ def cpu_oracle_rate(w, seconds=15.0, max_steps=20):
             more = min(more, max_steps - 1)
             if more > 0:
                 plan.append(more)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return npts * steps / elapsed / 1e9, steps, cores, elapsed
+    return npts * steps / elapsed / 1e9, steps, _oracle_threads(), elapsed
+
+
+def _oracle_threads():
+    """Threads the OpenMP oracle runs with: OMP_NUM_THREADS when set, else
+    the cores this process may run on (its CPU affinity, as nproc counts)."""
+    env = os.environ.get("OMP_NUM_THREADS", "")
+    if env.strip().isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _host_cpu():
+    """Model name of the host CPU (lscpu), for the baseline's description."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
 
 
 def run_reference(args, w, world, rank):
@@ -176,7 +203,7 @@ def run_reference(args, w, world, rank):
     for _ in range(args.steps):
         r, k, cores, el = cpu_oracle_rate(w, seconds=args.ref_seconds, max_steps=3)
         rates.append(r)
-        per.append(el / k * w["nt"] * 1e3)
+        per.append(el * 1e3)
     value = statistics.mean(rates)
     line = {
         "impl": "reference", "metric": "Gpts/s", "value": value, "unit": "Gpts/s",
@@ -185,9 +212,10 @@ def run_reference(args, w, world, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(w),
         "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{k} of {w['nt']} time steps of the full "
-                                   f"{'x'.join(map(str, _padded(w)))} grid per bench step; "
-                                   "ms_per_step extrapolated to the full run"},
+                         "cpu": _host_cpu(),
+                         "sample": f"one bench step = {k} of the workload's {w['nt']} time "
+                                   f"steps of the full {'x'.join(map(str, _padded(w)))} grid "
+                                   "(a bounded sample; ms_per_step is its measured time)"},
         "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -203,6 +231,30 @@ def _config(w):
             "nt": w["nt"], "nbl": w["nbl"], "receivers": len(w["rec"]),
             "l2": "inputs larger than L2 (each field 0.85 GB vs 129 MB L2); no flush",
             "parallelism": "replicas"}
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "acoustic_512_so8_1000.npz")
+
+
+def _parity(w, rec_dev):
+    """Relative L2 of the timed run's receivers against the FP64 oracle's
+    receivers of the same workload, stored by
+    tests/golden/make_acoustic_512_golden.py (the oracle is not run here);
+    None for workloads without stored receivers."""
+    if not os.path.exists(GOLDEN):
+        return None
+    gold = np.load(GOLDEN)
+    meta = json.loads(str(gold["meta"]))
+    if meta.get("workload") != w["name"] or w["space_order"] != 8:
+        return None
+    ref = gold["rec"].astype(np.float64)
+    got = rec_dev.double().cpu().numpy()
+    if got.shape != ref.shape:
+        return None
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"receivers_rel_l2": err, "tolerance": 1e-5, "pass": err <= 1e-5,
+            "against": "FP64 oracle receivers of the same workload "
+                       "(tests/golden/acoustic_512_so8_1000.npz)"}
 
 
 def run_ours(args, w, world, rank, local):
@@ -256,6 +308,7 @@ def run_ours(args, w, world, rank, local):
         ms = ev0.elapsed_time(ev1)
         info = g.info()
         g.set_profiling(False)
+        parity = _parity(w, rec_dev)
 
         # end to end through the public API with host buffers (pinned)
         e2e = None
@@ -293,9 +346,12 @@ def run_ours(args, w, world, rank, local):
             dist.destroy_process_group()
         return
     value = world * npts * nt * args.steps / (ms_max * 1e-3) / 1e9
-    avg_launch_ms = info["step_ms"] / max(1, info["steps_timed"])
+    blocked = info["schedule"] == 3
+    steps_per_launch = 2 if blocked else 1
+    launch_bytes = _LAUNCH_BYTES["temporal" if blocked else "single"] * npts
+    avg_launch_ms = steps_per_launch * info["step_ms"] / max(1, info["steps_timed"])
     peak, peak_kind = _peaks()
-    achieved = ALGO_BYTES_PER_POINT * npts / (avg_launch_ms * 1e-3) / 1e9
+    achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     line = {
         "metric": "Gpts/s", "value": value, "unit": "Gpts/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -305,9 +361,10 @@ def run_ours(args, w, world, rank, local):
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": _traffic(w["name"], [info["tile_x"], info["tile_y"]],
                                          _SCHED_NAME.get(info["schedule"])),
-                     "kernel": ("fd::sched_kernel" if info["schedule"] == 2 else
+                     "kernel": ("fd::tblock_kernel (two steps per launch)" if blocked else
+                                "fd::sched_kernel" if info["schedule"] == 2 else
                                 "fd::sweep_kernel") + " (avg over the timed launches)",
-                     "algorithmic_bytes_per_launch": ALGO_BYTES_PER_POINT * npts,
+                     "algorithmic_bytes_per_launch": launch_bytes,
                      "avg_launch_ms": avg_launch_ms},
         "clocks": clk,
         "gpu_launches": int(launches),
@@ -318,6 +375,8 @@ def run_ours(args, w, world, rank, local):
         "paper_context": {"value": 31.2, "unit": "Gpts/s",
                           "what": "SO 8 acoustic, 1x A100-80, 1158^3 + ABC, 290 steps"},
     }
+    if parity is not None:
+        line["parity"] = parity
     if e2e:
         line["e2e"] = {"value": world * npts * nt * args.steps / (e2e_max * 1e-3) / 1e9,
                        "unit": "Gpts/s", "h2d_bytes_per_step": e2e["h2d"],
@@ -325,6 +384,7 @@ def run_ours(args, w, world, rank, local):
     if not args.no_cpu_baseline and world == 1:
         r, k, cores, el = cpu_oracle_rate(w, seconds=args.ref_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+                                "cpu": _host_cpu(),
                                 "sample": f"{k} time steps of the full "
                                           f"{'x'.join(map(str, _padded(w)))} grid "
                                           f"({el:.1f} s)"}
@@ -444,9 +504,11 @@ def run_batched(args):
 
 def run_decomposed(args):
     """The headline grid cut into z slabs (fd_set_decomposition) in both
-    exchange modes, against the same grid undecomposed: Gpts/s of whole
-    fd_forward runs (device time, CUDA events), so the difference is what the
-    ghost planes, the halo copies and the extra launches cost on one GPU."""
+    exchange modes and into Cartesian boxes (fd_set_topology: the six face
+    messages packed in the step's epilogue, one unpack kernel per step),
+    against the same grid undecomposed: Gpts/s of whole fd_forward runs
+    (device time, CUDA events), so the difference is what the ghost layers,
+    the messages and the extra launches cost on one GPU."""
     import torch
     from paper_2312_13094_gb300 import binding as fd
     from paper_2312_13094_gb300 import workloads as wl
@@ -466,8 +528,15 @@ def run_decomposed(args):
         wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
         rec = torch.zeros((nt, len(w["rec"])), device="cuda")
         ref = None
-        for nsub, mode in [(1, 0)] + [(p, m) for p in args.slabs for m in (0, 1)]:
-            g.set_decomposition(nsub, mode)
+        cases = [(1, 0, None)] + [(p, m, None) for p in args.slabs for m in (0, 1)]
+        cases += [(1, 0, t) for t in args.topos]
+        for nsub, mode, topo in cases:
+            if topo is None:
+                g.set_topology(1, 1, 1)
+                g.set_decomposition(nsub, mode)
+            else:
+                g.set_decomposition(1)
+                g.set_topology(*topo)
             g.set_model(v_dev)
 
             def one():
@@ -484,10 +553,15 @@ def run_decomposed(args):
             else:
                 same = bool(torch.equal(rec, ref))
             gpts = npts * nt / (ms * 1e-3) / 1e9
-            rows.append({"slabs": nsub, "mode": ["basic", "overlap"][mode], "ms": ms,
-                         "gpts": gpts, "frac": 16 * gpts / peak,
-                         "launches_per_run": int(launches), "receivers_bitwise_equal": same})
+            row = {"slabs": nsub, "mode": ["basic", "overlap"][mode], "ms": ms,
+                   "gpts": gpts, "frac": 16 * gpts / peak,
+                   "launches_per_run": int(launches), "receivers_bitwise_equal": same}
+            if topo is not None:
+                row.update({"slabs": None, "topology": "x".join(map(str, topo)),
+                            "mode": "basic, boxes with the pack fused into the step"})
+            rows.append(row)
         g.set_decomposition(1)
+        g.set_topology(1, 1, 1)
         g.close()
     base = rows[0]["gpts"]
     for r in rows:
@@ -731,8 +805,11 @@ def main():
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "adjoint", "batched", "learned", "decomposed", "fwi",
                              "tti"])
-    ap.add_argument("--slabs", type=lambda t: [int(x) for x in t.split(",")], default=[2, 4, 8],
-                    help="decomposed workload: slab counts to time")
+    ap.add_argument("--slabs", type=lambda t: [int(x) for x in t.split(",") if x],
+                    default=[2, 4, 8], help="decomposed workload: slab counts to time")
+    ap.add_argument("--topos", default=[(2, 1, 1), (2, 2, 1), (1, 2, 2), (2, 2, 2)],
+                    type=lambda t: [tuple(int(v) for v in x.split("x")) for x in t.split(",") if x],
+                    help="decomposed workload: box topologies px x py x pz to time")
     ap.add_argument("--train-models", type=int, default=200)
     ap.add_argument("--test-models", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=20)

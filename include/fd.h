@@ -101,8 +101,9 @@ typedef struct {
   int64_t launches;               /* library kernels launched so far */
   double step_ms;                 /* summed device time of profiled steps */
   int64_t steps_timed;            /* steps inside that time */
-  int32_t schedule;               /* of the last forward run: FD_SCHED_SHARES or
-                                     FD_SCHED_WAVES (0 before the first run) */
+  int32_t schedule;               /* of the last forward run: FD_SCHED_SHARES,
+                                     FD_SCHED_WAVES or FD_SCHED_TEMPORAL (0 before
+                                     the first run) */
 } fd_grid_info;
 
 /* Creates a grid; allocates the two wavefields and the model on `device`.
@@ -206,6 +207,33 @@ fd_status fd_batch_forward(int32_t nshots, const fd_shot* shots,
 enum { FD_DMP_BASIC = 0, FD_DMP_OVERLAP = 1 };
 fd_status fd_set_decomposition(fd_grid grid, int32_t nsub, int32_t mode);
 
+/* Cartesian domain decomposition (Sec. III: a topology of px x py x pz ranks,
+ * each owning a box of the grid and exchanging an R-deep halo with its
+ * neighbours before every step).  The padded extents are split per axis into
+ * balanced ranges (sizes differ by at most one point); box (i, j, k), x
+ * fastest, keeps its two wavefields and model term with ghost layers (R
+ * rounded up to four floats in x, R in y and z), and every later
+ * fd_forward / fd_propagate on this grid steps all boxes in one launch per
+ * step.  The step writes, besides u^{n+1}, the updated points within R
+ * layers of each cut into the contiguous message of every neighbour they
+ * border (the pack is fused into the step); one unpack kernel then copies
+ * every message into the receiver's ghost block.  One message per face,
+ * edge and corner neighbour (the paper's diagonal mode: up to 26 per box):
+ * the stencil reads the faces, receivers next to an edge of a box also read
+ * edge and corner ghosts.  Every point is computed exactly as in the
+ * undecomposed run (receivers and wavefields equal bit for bit); the
+ * whole-grid state is scattered before a run and gathered after it.  All
+ * boxes live on the grid's device; across GPUs each message would be one
+ * peer copy (or NCCL send/recv) into the receiver's memory before the unpack.
+ * px = py = pz = 1 removes the topology; setting one removes any slabs of
+ * fd_set_decomposition and the reverse.  fd_adjoint_gradient, fd_backward and
+ * fd_batch_forward step the whole grid; temporal blocking is not applied to
+ * boxes.
+ * Errors: FD_ERR_ARG (a size < 1; a box thinner than R points along a split
+ * axis), FD_ERR_OOM, FD_ERR_CUDA; a run with per-cell or table weights
+ * returns FD_ERR_STATE. */
+fd_status fd_set_topology(fd_grid grid, int32_t px, int32_t py, int32_t pz);
+
 /* One model update of a full-waveform-inversion loop (the paper names FWI
  * as a user of the propagator, Sec. I and IV-B, without an update rule):
  * normalised steepest descent on n values,
@@ -256,11 +284,22 @@ fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas
  *                    on that device (fd_forward and fd_propagate; the pick is
  *                    cached per process; fd_grid_info shows the tile and
  *                    schedule in use).
+ *   FD_SCHED_TEMPORAL  temporal blocking (the paper's Discussion, Sec. IV,
+ *                    names it as future work): space orders 4 and 8 with
+ *                    uniform weights advance two steps per pass over the
+ *                    grid, reading u^{n-1}, u^n and the model once and
+ *                    writing u^{n+1} and u^{n+2} to a second pair of
+ *                    wavefield buffers (allocated on first use: two more
+ *                    grid fields); the first step is recomputed on an R-wide
+ *                    halo of each 56 x 24 (SO 8) or 56 x 28 (SO 4) tile.  An
+ *                    odd step count ends with one single step.  Other space
+ *                    orders, per-cell or table weights and decomposed grids
+ *                    run single steps with equal shares instead.
  * Adjoint and per-cell/table-weight steps always use equal shares on the
  * default tile; an explicit CTA count (fd_set_tile ctas > 0) uses equal
  * shares too.  Every schedule and tile gives the same results bit for bit.
  * Errors: FD_ERR_ARG (unknown mode). */
-enum { FD_SCHED_AUTO = 0, FD_SCHED_SHARES = 1, FD_SCHED_WAVES = 2 };
+enum { FD_SCHED_AUTO = 0, FD_SCHED_SHARES = 1, FD_SCHED_WAVES = 2, FD_SCHED_TEMPORAL = 3 };
 fd_status fd_set_schedule(fd_grid grid, int32_t mode);
 
 /* Test hooks, host-side fault injection only:
@@ -358,11 +397,15 @@ fd_status fd_mlp_make_samples(int32_t n, const float* prev, const float* cur, co
  *   wavelet  DEVICE [nt][src->n];  rec_out DEVICE [nt][rec->n]
  * Errors: FD_ERR_ARG when the padded grid and tables do not fit in the array
  * (the message gives the bytes needed) or an array is host memory; otherwise
- * as fd_set_model and fd_forward.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make it before any stream
- * capture.  All calls share the array and leave the last call's contents in
- * it; calls that overlap on the GPU race and must be serialised by the
- * caller. */
+ * as fd_set_model and fd_forward.  Each call whose stream is not being
+ * captured looks up the array's device address (cudaGetSymbolAddress), so a
+ * cudaDeviceReset by the caller between calls is harmless; a call on a
+ * capturing stream reuses the address found by the device's last call, so
+ * make the first call on a device before any stream capture.  Device waits
+ * give up after FD_SPIN_LIMIT clock cycles when that variable is set, as for
+ * fd_create_grid.  All calls share the array and leave the last call's
+ * contents in it; calls that overlap on the GPU race and must be serialised
+ * by the caller. */
 #define FD_NOALLOC_MAX_BYTES (32 * 1024 * 1024)
 fd_status fd_forward_noalloc(const fd_grid_desc* desc, const float* model, int32_t kind,
                              const fd_points* src, const float* wavelet,
@@ -422,6 +465,9 @@ fd_status fd_get_info(fd_grid grid, fd_grid_info* info);
 fd_status fd_set_profiling(fd_grid grid, int32_t enabled);
 /* Library-wide count of kernel launches issued so far. */
 int64_t fd_launch_count(void);
+/* Library-wide count of the device allocations (cudaMalloc) the library has
+ * made so far for grids, tables, staging and checkpoints. */
+int64_t fd_alloc_count(void);
 
 const char* fd_status_string(fd_status status);
 const char* fd_last_error(void); /* thread-local; "" when none */

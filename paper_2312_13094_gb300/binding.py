@@ -37,7 +37,7 @@ FD_DEBUG_SKIP_PLANE, FD_DEBUG_SPIN_LIMIT, FD_DEBUG_NO_GRAPH = 1, 2, 3
 FD_COEF_TAYLOR, FD_COEF_UNIFORM, FD_COEF_PER_CELL = 0, 1, 2
 FD_MLP_NPARAM, FD_MLP_SAMPLE = 5000, 10
 FD_DMP_BASIC, FD_DMP_OVERLAP = 0, 1
-FD_SCHED_AUTO, FD_SCHED_SHARES, FD_SCHED_WAVES = 0, 1, 2
+FD_SCHED_AUTO, FD_SCHED_SHARES, FD_SCHED_WAVES, FD_SCHED_TEMPORAL = 0, 1, 2, 3
 
 
 class fd_grid_desc(ctypes.Structure):
@@ -113,12 +113,14 @@ _SIGS = {
     "fd_set_tile": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_decomposition": (_S, [_G, ctypes.c_int32, ctypes.c_int32]),
     "fd_set_schedule": (_S, [_G, ctypes.c_int32]),
+    "fd_set_topology": (_S, [_G, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "fd_descent_step": (_S, [ctypes.c_int64, _P, _P, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "fd_set_debug": (_S, [_G, ctypes.c_int32, ctypes.c_int64]),
     "fd_get_info": (_S, [_G, ctypes.POINTER(fd_grid_info)]),
     "fd_set_profiling": (_S, [_G, ctypes.c_int32]),
     "fd_launch_count": (ctypes.c_int64, []),
+    "fd_alloc_count": (ctypes.c_int64, []),
     "fd_status_string": (ctypes.c_char_p, [_S]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
@@ -241,6 +243,9 @@ class Grid:
 
     def set_decomposition(self, nsub, mode=FD_DMP_BASIC):
         check(fd_set_decomposition(self.handle, nsub, mode), "fd_set_decomposition")
+
+    def set_topology(self, px, py, pz):
+        check(fd_set_topology(self.handle, px, py, pz), "fd_set_topology")
 
     def set_debug(self, key, value):
         check(fd_set_debug(self.handle, key, value), "fd_set_debug")

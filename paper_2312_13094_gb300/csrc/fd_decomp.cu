@@ -446,6 +446,7 @@ extern "C" fd_status fd_set_decomposition(fd_grid g, int32_t nsub, int32_t mode)
                 mode == FD_DMP_OVERLAP ? "overlap" : "basic");
   decomp_destroy(g);
   if (nsub == 1) return FD_OK;
+  cart_destroy(g);  // slabs and boxes exclude each other
 
   Decomp* d = new Decomp();
   d->nsub = nsub;

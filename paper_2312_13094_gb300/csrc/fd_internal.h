@@ -33,8 +33,10 @@ enum StepMode : int {
   kModeStoreE = 1,     // also e = (dt^2/m)(L u + s) for the imaging condition
   kModeAdjoint = 2,    // also grad -= u_cur * e_in / dt^2 (u_cur = z^{n+1})
   kModePerCell = 3,    // forward with per-cell weights c_1..c_R (space order 8)
-  kModeTable = 4       // forward with weights c_1..c_4 interpolated per point from a
+  kModeTable = 4,      // forward with weights c_1..c_4 interpolated per point from a
                        // table over A = (v dt / h)^2 (space order 8)
+  kModePack = 5        // forward, and the R updated layers next to each face of a
+                       // subdomain also written to that face's message buffer
 };
 
 // Everything one launch of the step kernel needs besides the tensor maps.
@@ -67,6 +69,20 @@ struct StepArgs {
   int32_t* err;              // device error word (bit 0: wait timed out)
   long long spin_limit;      // clock cycles before a wait gives up
   int32_t debug_skip_plane;  // test hook: never issue this plane's load (-1)
+  // Subdomain of a Cartesian decomposition (whole grids: 0, 0, Nx, Ny, 0, 0,
+  // 0): tiles start at array column xfirst and row yfirst, updated points lie
+  // below xend and yend, and the padded-grid coordinate of a point is its
+  // array coordinate plus (offx, offy, offz), which places the damping layer.
+  int32_t xfirst, yfirst, xend, yend;
+  int32_t offx, offy, offz;
+  // kModePack: message buffers towards the 26 neighbours, direction
+  // (dx, dy, dz) in {-1, 0, 1}^3 at index (dx+1) + 3 (dy+1) + 9 (dz+1)
+  // (nullptr: no neighbour there), and the owned extents.  A message holds
+  // the owned points next to that neighbour: along an axis with d = 0 the
+  // whole owned range, with d = -1 the first R layers, with d = +1 the last R,
+  // stored [z][y][x] over that block.
+  float* pack[27];
+  int32_t onx, ony, onz;
 };
 
 // One grid of a sweep launch (device memory): its tensor maps, constants and
@@ -104,6 +120,49 @@ struct StepOverride {
   const WorkItem* items;     // item_start[c+1]); nullptr: equal contiguous shares
 };
 
+// Two-step (temporally blocked) pass, fd_tblock.cuh: what does not change
+// from one pass to the next.  Source entries carry extended-tile coordinates
+// (lx, ly relative to the extended tile's corner); receiver entries are
+// relative to the output tile.
+struct TbArgs {
+  int32_t Nx, Ny, Nz, pitch, nbl, nx, ny, nz, tiles_x, tiles_y;
+  float bscale;
+  const int32_t* inj1_start;  // [tiles + 1]: step-1 sources, nodes of the extended tile
+  const InjEntry* inj1;
+  const int32_t* inj2_start;  // [tiles + 1]: step-2 sources, nodes of the output tile
+  const InjEntry* inj2;
+  const float* inj_val;       // [step][inj_ncol]
+  int32_t inj_ncol;
+  const int32_t* rec_start;   // [tiles + 1]
+  const RecEntry* recs;
+  float* rec_out;             // [step][rec_ncol]
+  int32_t rec_ncol;
+  const float* A;             // model term (step 2 reads its own points)
+  int32_t* err;
+};
+
+// Device descriptor of a two-step pass: tensor maps of the four wavefield
+// buffers (u^n with the two-step halo, extended tiles of u^{n-1}), of A, and
+// the buffers themselves.
+struct TbDesc {
+  CUtensorMap halo2[4];
+  CUtensorMap ext[4];
+  CUtensorMap extA;
+  float* u[4];
+  TbArgs args;
+};
+
+// Per-pass values: which buffers hold u^{n-1}, u^n and receive u^{n+1},
+// u^{n+2}; the value-table rows of the pass's first step; the work items.
+struct TbLaunch {
+  int in_prev, in_cur, out1, out2;
+  int inj_row, rec_row;
+  long long spin_limit;
+  float c[kMaxR + 1];
+  const int32_t* item_start;
+  const WorkItem* items;
+};
+
 struct TileShape {
   int tx, ty, pf;   // threads in x (4 points each), rows, prefetch depth
   int ctas;         // persistent CTAs per sweep (0: resident CTAs per SM x SMs)
@@ -116,5 +175,12 @@ cudaError_t launch_sweep_r(const TileShape& t, int mode, const ShotDesc* shots,
                            int grid, cudaStream_t s);
 template <int R>
 int sweep_blocks_per_sm_r(const TileShape& t, int mode);
+
+// Two-step passes (space orders 4 and 8), specialised in fd_step_r2.cu and
+// fd_step_r4.cu: the output tile and the launch.
+template <int R>
+void tblock_tile_r(int* bx, int* by);
+template <int R>
+cudaError_t launch_tblock_r(const TbDesc* d, const TbLaunch& l, int grid, cudaStream_t s);
 
 }  // namespace fd

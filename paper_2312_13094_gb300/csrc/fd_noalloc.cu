@@ -11,12 +11,14 @@
 // passes its inputs (model, wavelet) and output (receivers) in device memory.
 //
 // The array's name is only a host-side stand-in in host code; its device
-// address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) on the first call, which is why that first call should come
-// before any stream capture.  All calls share the one array and leave the last
-// call's contents behind; everything that must start at zero is cleared by the
-// call, and calls that overlap on the GPU (other threads, other streams) race
-// on the array.
+// address is looked up with cudaGetSymbolAddress (with the call's device
+// current) on every call whose stream is not being captured, so an address
+// made stale by a cudaDeviceReset of the caller is replaced; a call made while
+// its stream is being captured reuses the address of the device's last call,
+// which is why the first call on a device should come before any stream
+// capture.  All calls share the one array and leave the last call's contents
+// behind; everything that must start at zero is cleared by the call, and calls
+// that overlap on the GPU (other threads, other streams) race on the array.
 #include <string.h>
 
 #include <algorithm>
@@ -67,7 +69,10 @@ extern "C" fd_status fd_forward_noalloc(const fd_grid_desc* d, const float* mode
     return fail(FD_ERR_ARG, "fd_forward_noalloc takes device arrays only");
 
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[d->device]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(static_cast<cudaStream_t>(d->stream), &cap);
+  if (e) return cuda_fail(e, "stream capture query");
+  if (cap == cudaStreamCaptureStatusNone || !g_addr[d->device]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, fd_noalloc_scratch);
     if (e) return cuda_fail(e, "scratch symbol address");
@@ -87,7 +92,7 @@ extern "C" fd_status fd_forward_noalloc(const fd_grid_desc* d, const float* mode
   g.ncell = size_t(g.pitch) * g.Ny * g.Nz;
   fd_weights(g.R, g.c);
   g.cfl = cfl_limit(g.c, g.R);
-  g.spin_limit = 200000000LL;
+  g.spin_limit = default_spin_limit();
   g.no_graph = true;  // instantiating a graph allocates
   g.stream = static_cast<cudaStream_t>(d->stream);
   set_shape(&g, default_shape(g.R, g.Nx, g.Ny, g.Nz));

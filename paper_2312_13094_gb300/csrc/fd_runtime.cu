@@ -67,6 +67,19 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
+long long alloc_count() { return g_alloc_count.load(); }
+
+// Clock cycles a device-side wait spins before it gives up: ~0.1 s at 2 GHz
+// (a tile load takes microseconds), or FD_SPIN_LIMIT when set.
+long long default_spin_limit() {
+  long long v = 200000000LL;
+  if (const char* s = getenv("FD_SPIN_LIMIT")) {
+    const long long e = atoll(s);
+    if (e > 0) v = e;
+  }
+  return v;
+}
+
 cudaError_t DevBuf::ensure(size_t bytes) {
   if (bytes <= cap) return cudaSuccess;
   if (p) cudaFree(p);
@@ -294,7 +307,17 @@ struct PointCell {
   double f[3];
 };
 
+fd_status locate_point(fd_grid g, const float* xyz, int i0[3], double f[3]);
+
 static fd_status locate(fd_grid g, const float* xyz, PointCell* pc) {
+  return locate_point(g, xyz, pc->i0, pc->f);
+}
+
+// Padded floor node i0 and fractions f of a point given in metres from the
+// physical origin; FD_ERR_ARG outside the physical box.
+fd_status locate_point(fd_grid g, const float* xyz, int i0[3], double f[3]) {
+  PointCell c;
+  PointCell* pc = &c;
   const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
   for (int a = 0; a < 3; ++a) {
     const double s = double(xyz[a]) / g->d.h;
@@ -305,15 +328,23 @@ static fd_status locate(fd_grid g, const float* xyz, PointCell* pc) {
     pc->i0[a] = int(fl) + g->d.nbl;
     pc->f[a] = s - fl;
   }
+  for (int a = 0; a < 3; ++a) {
+    i0[a] = c.i0[a];
+    f[a] = c.f[a];
+  }
   return FD_OK;
 }
 
 // Trilinear injection entries of every point, scaled by `scale`, grouped per
-// tile and sorted by z within a tile.
-fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
-                          std::vector<int32_t>& start, std::vector<InjEntry>& out) {
-  const int bx = 4 * g->shape.tx, by = g->shape.ty;
-  const int ntiles = g->tiles_x * g->tiles_y;
+// tile and sorted by z within a tile (stable: a node's entries keep the order
+// of the points).  Tiles are bx x by; a tile's region is extended by hx
+// columns and hy rows on each side, so a node near a tile edge can belong to
+// several tiles, and lx, ly are relative to the extended region's corner.
+fd_status build_injection_tiles(fd_grid g, const fd_points* pts, double scale, int bx, int by,
+                                int hx, int hy, std::vector<int32_t>& start,
+                                std::vector<InjEntry>& out) {
+  const int tiles_x = (g->Nx + bx - 1) / bx, tiles_y = (g->Ny + by - 1) / by;
+  const int ntiles = tiles_x * tiles_y;
   std::vector<std::pair<int, InjEntry>> ent;
   for (int p = 0; p < (pts ? pts->n : 0); ++p) {
     PointCell pc;
@@ -329,14 +360,62 @@ fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
       }
       if (w == 0.0) continue;
       if (node[0] >= g->Nx || node[1] >= g->Ny || node[2] >= g->Nz) continue;
-      InjEntry e;
-      e.z = node[2];
-      e.lx = int16_t(node[0] % bx);
-      e.ly = int16_t(node[1] % by);
-      e.w = float(w * scale);
-      e.col = p;
-      ent.push_back({(node[1] / by) * g->tiles_x + node[0] / bx, e});
+      const int tx0 = std::max(0, (node[0] - hx) / bx);
+      const int tx1 = std::min(tiles_x - 1, (node[0] + hx) / bx);
+      const int ty0 = std::max(0, (node[1] - hy) / by);
+      const int ty1 = std::min(tiles_y - 1, (node[1] + hy) / by);
+      for (int ty = ty0; ty <= ty1; ++ty) {
+        for (int tx = tx0; tx <= tx1; ++tx) {
+          const int lx = node[0] - (tx * bx - hx), ly = node[1] - (ty * by - hy);
+          if (lx < 0 || lx >= bx + 2 * hx || ly < 0 || ly >= by + 2 * hy) continue;
+          InjEntry e;
+          e.z = node[2];
+          e.lx = int16_t(lx);
+          e.ly = int16_t(ly);
+          e.w = float(w * scale);
+          e.col = p;
+          ent.push_back({ty * tiles_x + tx, e});
+        }
+      }
     }
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
+    return a.first != b.first ? a.first < b.first : a.second.z < b.second.z;
+  });
+  start.assign(ntiles + 1, 0);
+  out.clear();
+  for (auto& e : ent) {
+    start[e.first + 1]++;
+    out.push_back(e.second);
+  }
+  for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
+  return FD_OK;
+}
+
+fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
+                          std::vector<int32_t>& start, std::vector<InjEntry>& out) {
+  return build_injection_tiles(g, pts, scale, 4 * g->shape.tx, g->shape.ty, 0, 0, start, out);
+}
+
+// Receivers grouped per bx x by tile (floor node's tile), sorted by z.
+fd_status build_receivers_tiles(fd_grid g, const fd_points* pts, int bx, int by,
+                                std::vector<int32_t>& start, std::vector<RecEntry>& out) {
+  const int tiles_x = (g->Nx + bx - 1) / bx, tiles_y = (g->Ny + by - 1) / by;
+  const int ntiles = tiles_x * tiles_y;
+  std::vector<std::pair<int, RecEntry>> ent;
+  for (int p = 0; p < (pts ? pts->n : 0); ++p) {
+    PointCell pc;
+    fd_status st = locate(g, pts->xyz + 3 * p, &pc);
+    if (st) return st;
+    RecEntry e;
+    e.z = pc.i0[2];
+    e.lx = int16_t(pc.i0[0] % bx);
+    e.ly = int16_t(pc.i0[1] % by);
+    e.fx = float(pc.f[0]);
+    e.fy = float(pc.f[1]);
+    e.fz = float(pc.f[2]);
+    e.col = p;
+    ent.push_back({(pc.i0[1] / by) * tiles_x + pc.i0[0] / bx, e});
   }
   std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
     return a.first != b.first ? a.first < b.first : a.second.z < b.second.z;
@@ -353,38 +432,11 @@ fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
 
 fd_status build_receivers(fd_grid g, const fd_points* pts, std::vector<int32_t>& start,
                           std::vector<RecEntry>& out) {
-  const int bx = 4 * g->shape.tx, by = g->shape.ty;
-  const int ntiles = g->tiles_x * g->tiles_y;
-  std::vector<std::pair<int, RecEntry>> ent;
-  for (int p = 0; p < (pts ? pts->n : 0); ++p) {
-    PointCell pc;
-    fd_status st = locate(g, pts->xyz + 3 * p, &pc);
-    if (st) return st;
-    RecEntry e;
-    e.z = pc.i0[2];
-    e.lx = int16_t(pc.i0[0] % bx);
-    e.ly = int16_t(pc.i0[1] % by);
-    e.fx = float(pc.f[0]);
-    e.fy = float(pc.f[1]);
-    e.fz = float(pc.f[2]);
-    e.col = p;
-    ent.push_back({(pc.i0[1] / by) * g->tiles_x + pc.i0[0] / bx, e});
-  }
-  std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
-    return a.first != b.first ? a.first < b.first : a.second.z < b.second.z;
-  });
-  start.assign(ntiles + 1, 0);
-  out.clear();
-  for (auto& e : ent) {
-    start[e.first + 1]++;
-    out.push_back(e.second);
-  }
-  for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
-  return FD_OK;
+  return build_receivers_tiles(g, pts, 4 * g->shape.tx, g->shape.ty, start, out);
 }
 
 template <class T>
-static fd_status upload(fd_grid g, DevBuf& buf, const std::vector<T>& v) {
+fd_status upload(fd_grid g, DevBuf& buf, const std::vector<T>& v) {
   cudaError_t e = buf.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
   if (e) return cuda_fail(e, "table allocation");
   if (!v.empty()) {
@@ -394,6 +446,9 @@ static fd_status upload(fd_grid g, DevBuf& buf, const std::vector<T>& v) {
   }
   return FD_OK;
 }
+template fd_status upload<int32_t>(fd_grid, DevBuf&, const std::vector<int32_t>&);
+template fd_status upload<InjEntry>(fd_grid, DevBuf&, const std::vector<InjEntry>&);
+template fd_status upload<RecEntry>(fd_grid, DevBuf&, const std::vector<RecEntry>&);
 
 fd_status upload_tables(fd_grid g, const fd_points* src, double src_scale,
                         const fd_points* rec, Tables& t) {
@@ -483,6 +538,8 @@ StepArgs base_args(fd_grid g) {
   a.tab_lo = g->tab_lo;
   a.tab_inv = g->tab_inv;
   a.tab_nodes = g->tab_nodes;
+  a.xend = g->Nx;
+  a.yend = g->Ny;
   return a;
 }
 
@@ -850,6 +907,8 @@ const char* fd_last_error(void) { return t_err.c_str(); }
 
 int64_t fd_launch_count(void) { return g_launches.load(); }
 
+int64_t fd_alloc_count(void) { return alloc_count(); }
+
 fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
   clear_error();
   if (!d || !out) return fail(FD_ERR_ARG, "null argument");
@@ -877,8 +936,7 @@ fd_status fd_create_grid(const fd_grid_desc* d, fd_grid* out) {
   g->ncell = size_t(g->pitch) * g->Ny * g->Nz;
   fd_weights(g->R, g->c);
   g->cfl = cfl_limit(g->c, g->R);
-  g->spin_limit = 200000000LL;  // ~0.1 s at 2 GHz; a tile load takes microseconds
-  if (const char* s = getenv("FD_SPIN_LIMIT")) g->spin_limit = atoll(s);
+  g->spin_limit = default_spin_limit();
   set_shape(g, default_shape(g->R, g->Nx, g->Ny, g->Nz));
   g->base_shape = g->shape;
   g->auto_tile = true;
@@ -929,6 +987,8 @@ fd_status fd_destroy_grid(fd_grid g) {
   cudaSetDevice(g->d.device);
   if (g->stream) cudaStreamSynchronize(g->stream);
   decomp_destroy(g);
+  cart_destroy(g);
+  tblock_destroy(g);
   if (g->graph_valid) cudaGraphExecDestroy(g->gexec);
   for (int b = 0; b < 2; ++b) {
     if (g->F.u[b]) cudaFree(g->F.u[b]);
@@ -1004,9 +1064,10 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
   const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;
   if ((nsrc && (!src->xyz || !wavelet)) || (nrec && (!rec->xyz || !rec_out)))
     return fail(FD_ERR_ARG, "points given without their data array");
-  fd_status st = use_shape(g, !g->dmp && forward_mode(g) == kModeForward);
+  fd_status st = use_shape(g, !g->dmp && !g->cart && forward_mode(g) == kModeForward);
   if (st) return st;
   if (g->dmp) return decomp_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
+  if (g->cart) return cart_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
   st = upload_tables(g, src, 1.0 / g->d.h, rec, g->tab);
   if (st) return st;
   const float* dval = nullptr;
@@ -1017,6 +1078,10 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
   if ((st = stage_out(g, g->stage_rec, nrec ? rec_out : nullptr, size_t(nsteps) * nrec,
                       &drec)))
     return st;
+  if (tblock_eligible(g) && nsteps >= 2) {
+    // two steps per pass (temporal blocking), fd_tblock.cu
+    if ((st = tblock_propagate(g, n0, nsteps, src, dval, rec, drec))) return st;
+  } else {
   RunSpec rs;
   memset(&rs, 0, sizeof(rs));
   rs.f = &g->F;
@@ -1040,6 +1105,7 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
     rs.rec_row_step = 1;
   }
   if ((st = run_steps(g, rs))) return st;
+  }
   if ((st = check_device_error(g))) return st;
   if (nrec) {
     if ((st = check_finite(g, drec, size_t(nsteps) * nrec))) return st;
@@ -1072,7 +1138,7 @@ fd_status fd_forward(fd_grid g, const fd_points* src, const float* wavelet,
   g->F.cur = 0;
   // plain forward runs of grids left on the default tile are tuned once, on
   // the zeroed wavefields, which are cleared again afterwards
-  if (g->auto_tile && !g->tuned && g->sched_mode == FD_SCHED_AUTO && !g->dmp &&
+  if (g->auto_tile && !g->tuned && g->sched_mode == FD_SCHED_AUTO && !g->dmp && !g->cart &&
       forward_mode(g) == kModeForward && g->d.nt >= kTuneMinSteps && g->debug_skip_plane < 0) {
     fd_status st = autotune_grid(g);
     if (st) return st;
@@ -1272,7 +1338,8 @@ fd_status fd_set_tile(fd_grid g, int32_t tile_x, int32_t tile_y, int32_t ctas) {
 fd_status fd_set_schedule(fd_grid g, int32_t mode) {
   clear_error();
   if (!g) return fail(FD_ERR_ARG, "null grid");
-  if (mode != FD_SCHED_AUTO && mode != FD_SCHED_SHARES && mode != FD_SCHED_WAVES)
+  if (mode != FD_SCHED_AUTO && mode != FD_SCHED_SHARES && mode != FD_SCHED_WAVES &&
+      mode != FD_SCHED_TEMPORAL)
     return fail(FD_ERR_ARG, "bad schedule %d", mode);
   g->sched_mode = mode;
   g->graph_valid = false;

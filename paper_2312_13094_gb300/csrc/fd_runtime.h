@@ -68,6 +68,8 @@ struct GraphKey {
 };
 
 struct Decomp;  // domain decomposition state of a grid (fd_decomp.cu)
+struct TbState;  // buffers of the two-step passes (fd_tblock.cu)
+struct Cart;     // boxes of a Cartesian decomposition (fd_cart.cu)
 
 constexpr int kNumShapes = 5;
 constexpr int kTuneMinSteps = 400;  // shorter forward runs are not worth tuning
@@ -118,6 +120,8 @@ struct fd_grid_s {
   cudaGraphExec_t gexec = nullptr;
   fd::GraphKey gkey = {};
   fd::Decomp* dmp = nullptr;  // z slabs of fd_set_decomposition (nullptr: whole grid)
+  fd::TbState* tb = nullptr;  // second wavefield pair etc. of FD_SCHED_TEMPORAL runs
+  fd::Cart* cart = nullptr;   // boxes of fd_set_topology (nullptr: not decomposed)
   int sched_mode = FD_SCHED_AUTO;  // fd_set_schedule
   fd::DevBuf sched;                // wave schedule: CTA starts, then the work items
   long long sched_key[5] = {};     // tile, grid and CTA count it was built for
@@ -137,6 +141,8 @@ fd_status fail(fd_status st, const char* fmt, ...);
 fd_status cuda_fail(cudaError_t e, const char* what);
 void clear_error();
 cudaError_t dev_alloc(void** p, size_t bytes);
+long long alloc_count();         // device allocations made through dev_alloc so far
+long long default_spin_limit();  // FD_SPIN_LIMIT, else ~0.1 s of clock cycles
 bool is_device_ptr(const void* p);
 fd_status make_map(CUtensorMap* m, const float* base, int Nx, int Ny, int Nz, int pitch, int bx,
                    int by);
@@ -170,6 +176,26 @@ fd_status build_injection(fd_grid g, const fd_points* pts, double scale,
                           std::vector<int32_t>& start, std::vector<InjEntry>& out);
 fd_status build_receivers(fd_grid g, const fd_points* pts, std::vector<int32_t>& start,
                           std::vector<RecEntry>& out);
+// Padded floor node and fractions of a point in metres (FD_ERR_ARG outside
+// the physical box).
+fd_status locate_point(fd_grid g, const float* xyz, int i0[3], double f[3]);
+// The same over bx x by tiles whose regions are widened by hx columns and hy
+// rows per side (entries relative to the widened region's corner).
+fd_status build_injection_tiles(fd_grid g, const fd_points* pts, double scale, int bx, int by,
+                                int hx, int hy, std::vector<int32_t>& start,
+                                std::vector<InjEntry>& out);
+fd_status build_receivers_tiles(fd_grid g, const fd_points* pts, int bx, int by,
+                                std::vector<int32_t>& start, std::vector<RecEntry>& out);
+// Host vector to a device buffer (grown as needed) on the grid's stream.
+template <class T>
+fd_status upload(fd_grid g, DevBuf& buf, const std::vector<T>& v);
+// Two-step passes (fd_tblock.cu): whether the grid's next forward run takes
+// them, the run itself (nsteps steps, the last one single-step when nsteps is
+// odd), and the release of their buffers with the grid.
+bool tblock_eligible(fd_grid g);
+fd_status tblock_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
+                           const float* dval, const fd_points* rec, float* drec);
+void tblock_destroy(fd_grid g);
 fd_status stage_in(fd_grid g, DevBuf& buf, const float* p, size_t n, const float** out);
 fd_status stage_out(fd_grid g, DevBuf& buf, float* p, size_t n, float** out);
 fd_status finish_out(fd_grid g, float* host, const float* dev, size_t n);
@@ -186,5 +212,10 @@ fd_status copy_field(fd_grid g, float* dev_field, void* user, int region, bool t
 fd_status decomp_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
                            const float* wavelet, const fd_points* rec, float* rec_out);
 void decomp_destroy(fd_grid g);
+// Cartesian boxes (fd_cart.cu): the steps of fd_forward / fd_propagate when
+// the grid has a px x py x pz topology, and the release of the boxes
+fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
+                         const float* wavelet, const fd_points* rec, float* rec_out);
+void cart_destroy(fd_grid g);
 
 }  // namespace fd

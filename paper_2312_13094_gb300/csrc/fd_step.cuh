@@ -180,6 +180,155 @@ __device__ __forceinline__ float lane(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// Lanes (0,1) (p = 0) or (2,3) (p = 1) of a float4 as a packed pair.
+__device__ __forceinline__ float2 half2of(const float4& v, int p) {
+  return p == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+}
+
+// Centre weight of the uniform stencil, -6 sum_{j>=1} c_j for the FP32
+// weights c_j, as an FP32 pair hi + lo (the sum is exact in FP64, and hi + lo
+// holds it to ~1e-15).  With hi alone the rounded centre weight leaves the
+// stencil a row sum of ~1e-7: the Laplacian of a constant field is then not
+// zero but that constant times a fixed bias, a spurious mass term whose phase
+// error grows with every step (about 1e-5 of the wavefield after 200 steps
+// at space order 8).  With the pair the residual is rounding noise without a
+// bias.
+template <int R>
+__device__ __forceinline__ void centre_weight(const float* c, float& hi, float& lo) {
+  double t = 0.0;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) t += static_cast<double>(c[j]);
+  t *= -6.0;
+  hi = static_cast<float>(t);
+  lo = static_cast<float>(t - static_cast<double>(hi));
+}
+
+// h^2 times the Laplacian of four consecutive x points with uniform weights:
+// lap = (hi + lo) u + sum_{j=1..R} c_j S_j, S_j the sum of the six neighbours
+// at distance j (centre_weight gives hi, lo).  Lanes (0,1) and (2,3) run as
+// packed pairs: each packed operation rounds every lane exactly as its scalar
+// form.  xr holds the row through the points (the points at xr[XO .. XO+3]),
+// yn(j, lo, hi) gives the float4s j rows below and above, zn(o) the float4 of
+// the plane at z offset o.
+template <int R, int XO, class YN, class ZN>
+__device__ __forceinline__ void lap4_packed(const float* xr, YN yn, ZN zn, const float* c,
+                                            float c0hi, float c0lo, float lap[4]) {
+  const float4 uc = zn(0);
+  const float2 hi2 = make_float2(c0hi, c0hi), lo2 = make_float2(c0lo, c0lo);
+  float2 lp[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 u2 = half2of(uc, p);
+    lp[p] = __ffma2_rn(hi2, u2, __fmul2_rn(lo2, u2));
+  }
+#pragma unroll
+  for (int jj = 1; jj <= R; ++jj) {
+    float4 ym, yp;
+    yn(jj, ym, yp);
+    const float4 zm = zn(-jj), zp = zn(jj);
+    const float2 cj = make_float2(c[jj], c[jj]);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int xa = XO + 2 * p - jj, xb = XO + 2 * p + jj;
+      // even distances pair aligned register halves; odd ones would
+      // straddle two and are summed lane by lane
+      const float2 sx =
+          (jj & 1) ? make_float2(__fadd_rn(xr[xa], xr[xb]), __fadd_rn(xr[xa + 1], xr[xb + 1]))
+                   : __fadd2_rn(make_float2(xr[xa], xr[xa + 1]), make_float2(xr[xb], xr[xb + 1]));
+      const float2 sy = __fadd2_rn(half2of(ym, p), half2of(yp, p));
+      const float2 sz = __fadd2_rn(half2of(zm, p), half2of(zp, p));
+      lp[p] = __ffma2_rn(cj, __fadd2_rn(__fadd2_rn(sx, sy), sz), lp[p]);
+    }
+  }
+  lap[0] = lp[0].x;
+  lap[1] = lp[0].y;
+  lap[2] = lp[1].x;
+  lap[3] = lp[1].y;
+}
+
+// Leapfrog update of four points where b = 0: u^{n+1} = A(lap + s) + (2u - u^{n-1})
+// with e = A(lap + s), as packed pairs (the roundings of the scalar form).
+__device__ __forceinline__ void update4_inner(const float lap[4], const float src[4],
+                                              const float4& uc, const float4& up,
+                                              const float4& Av, float res[4], float ev[4]) {
+  const float2 two = make_float2(2.0f, 2.0f);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 ls = __fadd2_rn(make_float2(lap[2 * p], lap[2 * p + 1]),
+                                 make_float2(src[2 * p], src[2 * p + 1]));
+    const float2 a2 = half2of(Av, p);
+    const float2 u2 = half2of(up, p);
+    const float2 e2 = __fmul2_rn(a2, ls);
+    const float2 r2 =
+        __ffma2_rn(a2, ls, __ffma2_rn(two, half2of(uc, p), make_float2(-u2.x, -u2.y)));
+    ev[2 * p] = e2.x;
+    ev[2 * p + 1] = e2.y;
+    res[2 * p] = r2.x;
+    res[2 * p + 1] = r2.y;
+  }
+}
+
+// The general damped update, (1+b) u^{n+1} = A(lap + s) + 2u - (1-b) u^{n-1},
+// b = bscale (dxx + dzz) per lane; lanes with ok[l] false give 0 (points
+// outside the grid).  For b = 0 it rounds exactly as update4_inner.
+__device__ __forceinline__ void update4_layer(const float lap[4], const float src[4],
+                                              const float4& uc4, const float4& up,
+                                              const float4& Av, const float dxx[4], float dzz,
+                                              float bscale, const bool ok[4], float res[4],
+                                              float ev[4]) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float b = bscale * (dxx[l] + dzz);
+    const float uc = lane(uc4, l);
+    const float ls = __fadd_rn(lap[l], src[l]);
+    const float e = __fmul_rn(lane(Av, l), ls);
+    float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
+    // inside the layer divide by 1+b (fast reciprocal; select, no branch)
+    const float td = __fdividef(t, 1.0f + b);
+    t = (b != 0.0f) ? td : t;
+    res[l] = ok[l] ? t : 0.0f;
+    ev[l] = ok[l] ? e : 0.0f;
+  }
+}
+
+// kModePack epilogue: the updated values of four owned points (owned
+// coordinates ox..ox+3, oy, oz) that lie within R layers of the box's faces
+// also go to the message of every neighbour they border: the face
+// neighbours, and the edge and corner neighbours where two or three faces
+// meet (the star stencil reads only faces, trilinear receivers near an edge
+// of the box also read edge and corner ghosts).
+template <int R>
+__device__ __forceinline__ void pack_faces(const StepArgs& a, const float res[4], int ox, int oy,
+                                           int oz) {
+  const bool ylo = oy < R, yhi = oy >= a.ony - R, zlo = oz < R, zhi = oz >= a.onz - R;
+  if (!(ox < R || ox + 3 >= a.onx - R || ylo || yhi || zlo || zhi)) return;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int x = ox + l;
+    if (x >= a.onx) break;
+    const bool xlo = x < R, xhi = x >= a.onx - R;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      if ((dz < 0 && !zlo) || (dz > 0 && !zhi)) continue;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        if ((dy < 0 && !ylo) || (dy > 0 && !yhi)) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          if ((dx < 0 && !xlo) || (dx > 0 && !xhi) || (dx == 0 && dy == 0 && dz == 0)) continue;
+          float* p = a.pack[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+          if (!p) continue;
+          const int ex = dx ? R : a.onx, ey = dy ? R : a.ony;
+          const int ix = dx > 0 ? x - (a.onx - R) : x;
+          const int iy = dy > 0 ? oy - (a.ony - R) : oy;
+          const int iz = dz > 0 ? oz - (a.onz - R) : oz;
+          p[(static_cast<size_t>(iz) * ey + iy) * ex + ix] = res[l];
+        }
+      }
+    }
+  }
+}
+
 // One CTA: the xy tile (tile_x, tile_y), output planes [zbeg, zend).  All
 // threads of the CTA must call this with the same arguments.
 //
@@ -213,8 +362,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const int tid = threadIdx.x;
   const int tx = tid % TX;
   const int ty = tid / TX;
-  const int x0 = tile_x * C::BX;
-  const int y0 = tile_y * C::BY;
+  const int x0 = a.xfirst + tile_x * C::BX;
+  const int y0 = a.yfirst + tile_y * C::BY;
   if (zbeg >= zend) return;
   const int zl = zend - zbeg;
   const int J = zl + 2 * R;  // u planes zbeg-R .. zend-1+R
@@ -321,23 +470,26 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
 
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx;
-    const bool in_grid = gy < a.Ny && gx < a.Nx;
-    const int dyv = sponge_depth(gy, a.nbl, a.ny);
+    const bool in_grid = gy < a.yend && gx < a.xend;
+    float c0hi = 0.f, c0lo = 0.f;
+    centre_weight<R>(ov.c, c0hi, c0lo);
+    // the layer in array coordinates (shifted for subdomains)
+    const int nblx = a.nbl - a.offx, nbly = a.nbl - a.offy, nblz = ov.nblz - a.offz;
+    const int dyv = sponge_depth(gy, nbly, a.ny);
     float dxx[4];
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-      const int d = sponge_depth(gx + l, a.nbl, a.nx);
+      const int d = sponge_depth(gx + l, nblx, a.nx);
       dxx[l] = static_cast<float>(d * d + dyv * dyv);
     }
-    const float c0x3 = 3.0f * ov.c[0];
     // planes [zf_lo, zf_hi) of this column have b = 0 at every point and no
     // point outside the grid: there the update needs no sponge terms or masks
-    int zf_lo = ov.nblz, zf_hi = ov.nblz + a.nz;
+    int zf_lo = nblz, zf_hi = nblz + a.nz;
     {
       const bool no_sponge = a.bscale == 0.0f;
-      const bool full = x0 + C::BX <= a.Nx && y0 + C::BY <= a.Ny;
-      const bool inner_xy = x0 >= a.nbl && x0 + C::BX <= a.nbl + a.nx && y0 >= a.nbl &&
-                            y0 + C::BY <= a.nbl + a.ny;
+      const bool full = x0 + C::BX <= a.xend && y0 + C::BY <= a.yend;
+      const bool inner_xy = x0 >= nblx && x0 + C::BX <= nblx + a.nx && y0 >= nbly &&
+                            y0 + C::BY <= nbly + a.ny;
       if (no_sponge) {
         zf_lo = zbeg;
         zf_hi = zend;
@@ -379,10 +531,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           xr[4 * m + 3] = v.w;
         }
         float lap[4];
+        // per-point weights: lap = sum_j c_j (S_j - 6u), so no FP32 centre weight
+        // carries a rounding bias into the row sum
         if (MODE == kModePerCell || MODE == kModeTable) {
-          // per-point weights c_1..c_R, c_0 = -2 sum_j c_j: from the staged
-          // coefficient tiles, or interpolated linearly in the table at the
-          // point's own A = (v dt / h)^2
+          // per-point weights c_1..c_R: from the staged coefficient tiles, or
+          // interpolated linearly in the table at the point's own
+          // A = (v dt / h)^2
           float ct[4][R];
           if (MODE == kModeTable) {
             const float4 At = *reinterpret_cast<const float4*>(abuf + sa * C::TPITCH + ctile);
@@ -399,7 +553,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                 ct[l][jj - 1] = fmaf(f, lane(dt, jj - 1), lane(t0, jj - 1));
             }
           }
-          float cs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int jj = 1; jj <= R; ++jj) {
             float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -414,28 +567,18 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
               const float sy = lane(ym, l) + lane(yp, l);
               const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
               const float cj = (MODE == kModeTable) ? ct[l][jj - 1] : lane(cv, l);
-              cs[l] += cj;
-              lap[l] = (jj == 1) ? cj * ((sx + sy) + sz) : fmaf(cj, (sx + sy) + sz, lap[l]);
+              const float d = fmaf(-6.0f, xr[C::RX + l], (sx + sy) + sz);
+              lap[l] = (jj == 1) ? cj * d : fmaf(cj, d, lap[l]);
             }
           }
-#pragma unroll
-          for (int l = 0; l < 4; ++l) lap[l] = fmaf(-6.0f * cs[l], xr[C::RX + l], lap[l]);
         } else {
-#pragma unroll
-          for (int l = 0; l < 4; ++l) lap[l] = c0x3 * xr[C::RX + l];
-#pragma unroll
-          for (int jj = 1; jj <= R; ++jj) {
-            const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
-            const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
-            const float cj = ov.c[jj];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-              const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
-              const float sy = lane(ym, l) + lane(yp, l);
-              const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
-              lap[l] = fmaf(cj, (sx + sy) + sz, lap[l]);
-            }
-          }
+          lap4_packed<R, C::RX>(
+              xr,
+              [&](int jj, float4& ym, float4& yp) {
+                ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
+                yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+              },
+              [&](int o) { return FD_Q(o); }, ov.c, c0hi, c0lo, lap);
         }
 
         // point sources of this plane (owner thread adds its share)
@@ -462,28 +605,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         // that a recomputed segment reproduces the stored states bit for bit
         if (k >= zf_lo && k < zf_hi) {
           // b = 0: (1-b) = 1 and no division; every column is inside the grid
-#pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            const float ls = __fadd_rn(lap[l], src[l]);
-            ev[l] = __fmul_rn(lane(Av, l), ls);
-            res[l] = fmaf(lane(Av, l), ls, fmaf(2.0f, lane(FD_Q(0), l), -lane(up, l)));
-          }
+          update4_inner(lap, src, FD_Q(0), up, Av, res, ev);
         } else {
-          const int dz = sponge_depth(k, ov.nblz, a.nz);
-          const float dzz = static_cast<float>(dz * dz);
-#pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            const float b = a.bscale * (dxx[l] + dzz);
-            const float uc = lane(FD_Q(0), l);
-            const float ls = __fadd_rn(lap[l], src[l]);
-            const float e = __fmul_rn(lane(Av, l), ls);
-            float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
-            // inside the layer divide by 1+b (fast reciprocal; select, no branch)
-            const float td = __fdividef(t, 1.0f + b);
-            t = (b != 0.0f) ? td : t;
-            res[l] = (gx + l < a.Nx) ? t : 0.0f;
-            ev[l] = (gx + l < a.Nx) ? e : 0.0f;
-          }
+          const int dz = sponge_depth(k, nblz, a.nz);
+          const bool ok[4] = {gx < a.xend, gx + 1 < a.xend, gx + 2 < a.xend, gx + 3 < a.xend};
+          update4_layer(lap, src, FD_Q(0), up, Av, dxx, static_cast<float>(dz * dz), a.bscale, ok,
+                        res, ev);
         }
         if (in_grid) {
           st_stream(out + off, res[0], res[1], res[2], res[3]);
@@ -499,6 +626,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             g.w -= uc.w * ein.w * a.inv_dt2;
             *reinterpret_cast<float4*>(a.grad + off) = g;
           }
+          if (MODE == kModePack) pack_faces<R>(a, res, gx - a.xfirst, gy - a.yfirst, k - ov.zfirst);
         }
         off += plane_stride;
 

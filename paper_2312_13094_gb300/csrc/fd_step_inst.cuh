@@ -4,6 +4,9 @@
 #pragma once
 
 #include "fd_step.cuh"
+#if FD_R == 2 || FD_R == 4
+#include "fd_tblock.cuh"
+#endif
 
 namespace fd {
 namespace {
@@ -121,6 +124,8 @@ cudaError_t launch_sweep_r<FD_R>(const TileShape& t, int mode, const ShotDesc* s
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 1>(shots, prefix, nshots, ov, grid, s); \
       case kModeAdjoint:                                                                  \
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(shots, prefix, nshots, ov, grid, s); \
+      case kModePack:                                                                     \
+        return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 5>(shots, prefix, nshots, ov, grid, s); \
       FD_PERCELL_LAUNCH(TX, TY)                                                           \
       default: return cudaErrorInvalidValue;                                              \
     }                                                                                     \
@@ -138,6 +143,7 @@ int sweep_blocks_per_sm_r<FD_R>(const TileShape& t, int mode) {
       case kModeForward: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 0>(); \
       case kModeStoreE: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 1>();  \
       case kModeAdjoint: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(); \
+      case kModePack: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 5>();    \
       FD_PERCELL_OCC(TX, TY)                                                    \
       default: return 0;                                                        \
     }                                                                           \
@@ -146,5 +152,29 @@ int sweep_blocks_per_sm_r<FD_R>(const TileShape& t, int mode) {
 #undef FD_SHAPE
   return 0;
 }
+
+#if FD_R == 2 || FD_R == 4
+template <>
+void tblock_tile_r<FD_R>(int* bx, int* by) {
+  *bx = TbGeom<FD_R>::BX;
+  *by = TbGeom<FD_R>::BY;
+}
+
+template <>
+cudaError_t launch_tblock_r<FD_R>(const TbDesc* d, const TbLaunch& l, int grid, cudaStream_t s) {
+  static unsigned long long done = 0;  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!(done & (1ull << (dev & 63)))) {
+    cudaError_t e = cudaFuncSetAttribute(tblock_kernel<FD_R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TbGeom<FD_R>::SMEM);
+    if (e != cudaSuccess) return e;
+    done |= 1ull << (dev & 63);
+  }
+  tblock_kernel<FD_R><<<grid, TbGeom<FD_R>::NT, TbGeom<FD_R>::SMEM, s>>>(d, l);
+  return cudaGetLastError();
+}
+#endif
 
 }  // namespace fd

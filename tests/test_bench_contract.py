@@ -26,3 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"].startswith("acoustic 24^3 SO8")
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"]
+    # a bench step of this arm is the timed sample itself, not an extrapolation
+    assert 0 < d["ms_per_step"] < 600_000
+    if not os.environ.get("OMP_NUM_THREADS"):
+        assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert "measured time" in d["cpu_baseline"]["sample"]

@@ -141,3 +141,45 @@ def test_autograd_function_gives_the_oracle_gradient(fd):
     assert abs(float(loss.detach()) - rloss) <= 1e-5 * abs(rloss)
     grad = m.grad.cpu().numpy()
     assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_directional_derivative_on_the_configured_grid(fd):
+    """The gradient workload as configured: 256^3 + 20-cell layer, SO 8, 500
+    steps, 25 checkpoints, observed data from the Gaussian-anomaly model and
+    the gradient at the start model v = 2.0.  <g, dm> against the central
+    difference (J(m0 + e dm) - J(m0 - e dm)) / 2e with e = 1e-3 and
+    dm = m0 * phi, phi the anomaly's Gaussian shape, both from the GPU path."""
+    import torch
+    w = wl.adjoint_256()
+    w0 = wl.adjoint_256(anomaly=False)
+    wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
+    nrec = len(w["rec"])
+
+    def forward(model, kind):
+        with fd.Grid.from_workload(w) as g:
+            g.set_model(model, kind)
+            rec = torch.zeros((w["nt"], nrec), device="cuda")
+            fd.check(g.forward(w["src"], wav, w["rec"], rec), "fd_forward")
+            return rec.double()
+
+    d_obs = forward(torch.from_numpy(w["v"]).cuda(), fd.FD_MODEL_VP_KMS)
+    m0 = torch.from_numpy((1.0 / w0["v"].astype(np.float64) ** 2)).cuda()
+    phi = torch.from_numpy(w["shape"].astype(np.float64)).cuda()
+    dm = m0 * phi
+    with fd.Grid.from_workload(w) as g:
+        g.set_model(m0.float().contiguous(), fd.FD_MODEL_M)
+        grad = torch.zeros(g.phys_shape, device="cuda")
+        st, loss = g.adjoint_gradient(w["src"], wav, w["rec"], d_obs.float().contiguous(), 25,
+                                      grad)
+        fd.check(st, "fd_adjoint_gradient")
+    eps = 1e-3
+    losses = []
+    for sgn in (1, -1):
+        rec = forward((m0 + sgn * eps * dm).float().contiguous(), fd.FD_MODEL_M)
+        losses.append(0.5 * float(((rec - d_obs) ** 2).sum()))
+    fd_dir = (losses[0] - losses[1]) / (2 * eps)
+    ad_dir = float((grad.double() * dm).sum())
+    gap = abs(fd_dir - ad_dir) / abs(ad_dir)
+    print(f"296^3 x 500, 25 checkpoints: <g, dm> {ad_dir:.6e}, central difference "
+          f"{fd_dir:.6e}, relative gap {gap:.2e}")
+    assert gap <= 2e-3, (fd_dir, ad_dir)

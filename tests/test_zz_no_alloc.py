@@ -90,3 +90,66 @@ def test_host_arrays_are_rejected(fd):
     st = fd.fd_forward_noalloc(ctypes.byref(desc), w["v"].ctypes.data, fd.FD_MODEL_VP_KMS, None,
                                None, None, None)
     assert st == fd.FD_ERR_ARG
+
+
+def test_calls_allocate_nothing_on_a_caller_stream(fd):
+    """Several sources and receivers on a stream the caller created: the
+    entry point matches fd_forward on the same stream, its calls leave the
+    library's device allocation count and the device's free memory
+    unchanged, and a call made while the library's next allocation is set to
+    fail (FD_FAULT_ALLOC_AT) still succeeds."""
+    import os
+    import torch
+    w = _workload(8, (36, 30, 28), 50, 5)
+    ext = [(d - 1) * w["h"] for d in w["n"]]
+    w["src"] = np.array([[0.3 * ext[0], 0.4 * ext[1], 0.5 * ext[2]],
+                         [0.71 * ext[0], 0.22 * ext[1], 0.35 * ext[2]],
+                         [ext[0], 0.0, 0.8 * ext[2]]])
+    f = [25.0, 18.0, 30.0]
+    w["wavelet"] = np.ascontiguousarray(
+        np.stack([wl.ricker(w["nt"], w["dt"], fh) for fh in f], 1), np.float32)
+    w["rec"] = np.array([[x, y, 2.5 * w["h"]] for x in np.linspace(0.0, ext[0], 8)
+                         for y in np.linspace(0.0, ext[1], 5)])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with fd.Grid.from_workload(w, stream=stream.cuda_stream) as g:
+            g.set_model(w["v"])
+            ref = np.zeros((w["nt"], len(w["rec"])), np.float32)
+            fd.check(g.forward(w["src"], w["wavelet"], w["rec"], ref), "fd_forward")
+        desc = fd.fd_grid_desc(*[int(x) for x in w["n"]], float(w["h"]), int(w["space_order"]),
+                               int(w["nbl"]), float(w["dt"]), int(w["nt"]), 0,
+                               stream.cuda_stream)
+        v = torch.from_numpy(w["v"]).cuda()
+        wav = torch.from_numpy(w["wavelet"]).cuda()
+        outs = [torch.full((w["nt"], len(w["rec"])), float("nan"), device="cuda")
+                for _ in range(3)]
+        s, r = fd.Points(w["src"]), fd.Points(w["rec"])
+        torch.cuda.synchronize()
+
+        def call(out):
+            st = fd.fd_forward_noalloc(ctypes.byref(desc), v.data_ptr(), fd.FD_MODEL_VP_KMS,
+                                       s.ref(), wav.data_ptr(), r.ref(), out.data_ptr())
+            fd.check(st, "fd_forward_noalloc")
+
+        call(outs[0])  # loads the kernels the call uses (lazy module loading)
+        torch.cuda.synchronize()
+        allocs0 = fd.fd_alloc_count()
+        free0 = torch.cuda.mem_get_info()[0]
+        call(outs[1])
+        key = "FD_FAULT_ALLOC_AT"
+        old = os.environ.get(key)
+        os.environ[key] = str(fd.fd_alloc_count() + 1)
+        try:
+            call(outs[2])
+        finally:
+            if old is None:
+                del os.environ[key]
+            else:
+                os.environ[key] = old
+        torch.cuda.synchronize()
+        assert fd.fd_alloc_count() == allocs0
+        assert torch.cuda.mem_get_info()[0] == free0
+    for out in outs:
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL
