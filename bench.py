@@ -236,24 +236,33 @@ def _config(w):
 GOLDEN = os.path.join(ROOT, "tests", "golden", "acoustic_512_so8_1000.npz")
 
 
-def _parity(w, rec_dev):
-    """Relative L2 of the timed run's receivers against the FP64 oracle's
-    receivers of the same workload, stored by
-    tests/golden/make_acoustic_512_golden.py (the oracle is not run here);
-    None for workloads without stored receivers."""
+def _parity(w, g):
+    """Relative L2 of the timed run's last two wavefields against the FP64
+    oracle run of the same workload at the cells it stored
+    (tests/golden/make_acoustic_512_golden.py; the oracle is not run here);
+    None for workloads without a stored run.  (The workload's receivers see
+    no arrival within its 1000 steps, so the wavefields carry the check.)"""
     if not os.path.exists(GOLDEN):
         return None
     gold = np.load(GOLDEN)
     meta = json.loads(str(gold["meta"]))
     if meta.get("workload") != w["name"] or w["space_order"] != 8:
         return None
-    ref = gold["rec"].astype(np.float64)
-    got = rec_dev.double().cpu().numpy()
-    if got.shape != ref.shape:
-        return None
-    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    return {"receivers_rel_l2": err, "tolerance": 1e-5, "pass": err <= 1e-5,
-            "against": "FP64 oracle receivers of the same workload "
+    import torch
+    from paper_2312_13094_gb300 import binding as fd
+    prev = torch.zeros(g.phys_shape, device="cuda")
+    cur = torch.zeros(g.phys_shape, device="cuda")
+    g.get_wavefield(prev, cur, fd.FD_REGION_PHYSICAL)
+    pts = torch.from_numpy(gold["pts"].astype(np.int64)).cuda()
+    e = []
+    for field, key in ((cur, "u_last"), (prev, "u_prev")):
+        got = field[pts[:, 0], pts[:, 1], pts[:, 2]].double().cpu().numpy()
+        ref = gold[key]
+        e.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    del prev, cur
+    return {"wavefield_rel_l2": e[0], "previous_wavefield_rel_l2": e[1], "tolerance": 1e-5,
+            "pass": max(e) <= 1e-5, "cells": int(len(gold["pts"])),
+            "against": "FP64 oracle run of the same workload, sampled cells "
                        "(tests/golden/acoustic_512_so8_1000.npz)"}
 
 
@@ -308,7 +317,7 @@ def run_ours(args, w, world, rank, local):
         ms = ev0.elapsed_time(ev1)
         info = g.info()
         g.set_profiling(False)
-        parity = _parity(w, rec_dev)
+        parity = _parity(w, g)
 
         # end to end through the public API with host buffers (pinned)
         e2e = None
@@ -762,6 +771,15 @@ def run_learned(args):
         t1 = time.time()
         l1 = net.train(S, epochs=args.epochs, batch=65536, lr=1e-3)
         t_train = time.time() - t1
+    ft = None
+    if args.finetune:
+        rows0 = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt,
+                            ladder=False)
+        hist, beta = lr.finetune_output_bias(net, range(args.finetune), n=n, nt=nt)
+        ft = {"train_models": args.finetune, "max_rel_l2_history": hist,
+              "bias_shift": [float(b) for b in beta],
+              "held_out_before": {"mean": float(np.mean([r["learned_table"] for r in rows0])),
+                                  "max": float(np.max([r["learned_table"] for r in rows0]))}}
     rows = lr.evaluate(net, range(10000, 10000 + args.test_models), n=n, nt=nt,
                        ladder=args.ladder)
     os.makedirs(_out_dir(), exist_ok=True)
@@ -775,11 +793,39 @@ def run_learned(args):
     def mean(key):
         return float(np.mean([r[key] for r in rows]))
 
+    def worst(key):
+        return float(np.max([r[key] for r in rows]))
+
+    # the criterion, fixed before measuring: EVERY held-out model within 1 %
+    # receiver relative L2 of the fine SO 16 solve; among the configurations
+    # that meet it, the least mean GPU time per run wins
+    limit = 0.01
+    configs = {"learned coarse h20 SO8 dt1.6 (weight table)": ("learned_table",
+                                                               "ms_learned_table"),
+               "learned coarse h20 SO8 dt1.6 (per-cell weights)": ("learned", "ms_learned"),
+               "plain coarse h20 SO8 dt1.6": ("plain", "ms_plain"),
+               "plain coarse h20 SO16 dt1.6": ("plain16", "ms_plain16")}
     ladder = {}
     if args.ladder:
-        for (hh, so, _) in lr.LADDER:
+        for (hh, so, dt) in lr.LADDER:
             key = f"h{hh:.4g}_so{so}"
-            ladder[key] = {"rel_l2": mean(key), "ms": mean("ms_" + key)}
+            ladder[key] = {"rel_l2": mean(key), "max_rel_l2": worst(key), "ms": mean("ms_" + key)}
+            configs[f"plain h{hh:.4g} SO{so} dt{dt:g}"] = (key, "ms_" + key)
+    table = {name: {"mean_rel_l2": mean(k), "max_rel_l2": worst(k),
+                    "models_within": int(sum(r[k] <= limit for r in rows)),
+                    "passes": worst(k) <= limit, "ms": mean(t)}
+             for name, (k, t) in configs.items()}
+    plain_pass = {n: v for n, v in table.items() if n.startswith("plain") and v["passes"]}
+    cheapest = min(plain_pass, key=lambda n: plain_pass[n]["ms"]) if plain_pass else None
+    lt = table["learned coarse h20 SO8 dt1.6 (weight table)"]
+    verdict = {
+        "criterion": "every held-out model: receiver rel. L2 vs the fine SO 16 solve <= 1 %; "
+                     "then least GPU time per run",
+        "learned_passes": lt["passes"], "learned_max_rel_l2": lt["max_rel_l2"],
+        "learned_ms": lt["ms"], "cheapest_plain_passing": cheapest,
+        "cheapest_plain_passing_ms": plain_pass[cheapest]["ms"] if cheapest else None,
+        "learned_wins": bool(lt["passes"] and (cheapest is None or
+                                               lt["ms"] < plain_pass[cheapest]["ms"]))}
     plain = mean("plain")
     learned = mean("learned_table")
     print(json.dumps({
@@ -792,7 +838,7 @@ def run_learned(args):
         "ms_coarse_plain": mean("ms_plain"),
         "ms_coarse_learned_percell": mean("ms_learned"),
         "ms_coarse_learned": mean("ms_learned_table"),
-        "plain_ladder": ladder,
+        "plain_ladder": ladder, "configurations": table, "verdict": verdict, "finetune": ft,
         "loss_before": l0, "loss_after": l1, "samples": int(S.shape[0]),
         "train_models": args.train_models, "test_models": args.test_models,
         "epochs": args.epochs, "data_s": t_data, "train_s": t_train, "rows": rows,
@@ -816,6 +862,9 @@ def main():
     ap.add_argument("--params", default="",
                     help="learned workload: evaluate a trained network (checkpoint or .npy), "
                          "no training")
+    ap.add_argument("--finetune", type=int, default=0,
+                    help="learned workload: fine-tune the output bias on the receiver misfit "
+                         "of this many training models (0: none)")
     ap.add_argument("--ladder", action="store_true",
                     help="learned workload: also time plain SO 8/16 at h 16 and 12.8 m")
     ap.add_argument("--gpus", type=int, default=1)

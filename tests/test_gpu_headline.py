@@ -11,9 +11,9 @@ Sec. IV-C and the off-grid points of Sec. III "Sparse data").
   SO 16 on its tuned 32 x 16 tile: receivers and final wavefield against the
   FP64 oracle run, relative L2 <= 1e-5.
 * The full headline run (592^3, 1000 steps) in the benchmark's own
-  configuration (tile and schedule picked by the tuner): its receivers and
-  sampled cells of the final state against the FP64 oracle's, written once by
-  ``tests/golden/make_acoustic_512_golden.py`` (oracle only).
+  configuration (tile and schedule picked by the tuner): sampled cells of its
+  last two wavefields (and its receivers) against the FP64 oracle's, written
+  once by ``tests/golden/make_acoustic_512_golden.py`` (oracle only).
 """
 import json
 import os
@@ -95,11 +95,17 @@ def test_reduced_headline_schedules_agree_bitwise(fd, reduced):
     np.testing.assert_array_equal(a[1], b[1])
 
 
-@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden receivers not written")
-def test_full_headline_run_against_the_oracle_receivers(fd):
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden oracle run not written")
+def test_full_headline_run_against_the_oracle(fd):
     """592^3, SO 8, 1000 steps in the benchmark's configuration (default tile
-    and schedule, tuned by the first long run) against the stored FP64
-    oracle receivers and sampled final-state cells."""
+    and schedule, tuned by the first long run) against the stored FP64 oracle
+    run: the final and previous wavefields at 18k sampled cells (random cells,
+    the source's and the receiver line's neighbourhoods, corners, faces) within
+    relative L2 1e-5.  The receivers sit 2.5 km from the source and the direct
+    wave needs ~1.7 s to reach them, longer than the workload's 1.27 s: they
+    hold only the stencil's numerical precursor (~1e-33), so they are held to
+    the oracle's values within 1e-5 of the wavefield's amplitude instead of a
+    relative norm."""
     import torch
     gold = np.load(GOLDEN)
     meta = json.loads(str(gold["meta"]))
@@ -108,16 +114,24 @@ def test_full_headline_run_against_the_oracle_receivers(fd):
     with fd.Grid.from_workload(w) as g:
         g.set_model(torch.from_numpy(w["v"]).cuda())
         rec = torch.zeros((w["nt"], len(w["rec"])), device="cuda")
-        u = torch.zeros(g.phys_shape, device="cuda")
         wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
-        fd.check(g.forward(w["src"], wav, w["rec"], rec, u), "fd_forward")
+        fd.check(g.forward(w["src"], wav, w["rec"], rec), "fd_forward")
         info = g.info()
+        prev = torch.zeros(g.phys_shape, device="cuda")
+        cur = torch.zeros(g.phys_shape, device="cuda")
+        g.get_wavefield(prev, cur, fd.FD_REGION_PHYSICAL)
         torch.cuda.synchronize()
     pts = torch.from_numpy(gold["pts"].astype(np.int64)).cuda()
-    got_u = u[pts[:, 0], pts[:, 1], pts[:, 2]].cpu().numpy()
-    rec = rec.cpu().numpy()
-    e_rec = rel(rec, gold["rec"].astype(np.float64))
+    got_u = cur[pts[:, 0], pts[:, 1], pts[:, 2]].cpu().numpy()
+    got_p = prev[pts[:, 0], pts[:, 1], pts[:, 2]].cpu().numpy()
+    rec = rec.cpu().numpy().astype(np.float64)
     e_u = rel(got_u, gold["u_last"])
+    e_p = rel(got_p, gold["u_prev"])
+    scale = np.abs(gold["u_last"]).max()
+    e_rec = np.abs(rec - gold["rec"]).max() / scale
     print(f"592^3 x 1000 (tile {info['tile_x']}x{info['tile_y']}, schedule "
-          f"{info['schedule']}): receivers {e_rec:.2e}, sampled final state {e_u:.2e}")
-    assert e_rec <= TOL and e_u <= TOL
+          f"{info['schedule']}): sampled u^1000 {e_u:.2e}, u^999 {e_p:.2e}; receivers "
+          f"max |error| / max |u| {e_rec:.1e} (oracle receivers up to "
+          f"{np.abs(gold['rec']).max():.1e})")
+    assert e_u <= TOL and e_p <= TOL
+    assert e_rec <= TOL
