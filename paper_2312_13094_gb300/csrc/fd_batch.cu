@@ -89,7 +89,7 @@ struct Prepared {
   int ctas = 0;
   bool waves = false;
   size_t off_start = 0, off_items = 0;  // wave schedule within `host`
-  float c[kMaxR + 1] = {};  // stencil weights (the same for every shot)
+  float c[kMaxR + 2] = {};  // stencil weights (the same for every shot; launch_weights)
   int nbl = 0;              // layer width (the same for every shot)
   long long spin_limit = 0;
 };
@@ -165,7 +165,7 @@ fd_status prepare(int nshots, const fd_shot* shots, const TileShape& t, bool wav
     memcpy(P.host.data() + P.off_items, items.data(), items.size() * sizeof(WorkItem));
   }
   fd_grid g0 = shots[0].grid;
-  for (int j = 0; j <= kMaxR; ++j) P.c[j] = j <= R ? float(g0->c[j]) : 0.0f;
+  launch_weights(g0->c, R, P.c);
   P.spin_limit = g0->spin_limit;
   P.nbl = g0->d.nbl;
   return FD_OK;
@@ -208,7 +208,7 @@ fd_status issue_steps(BatchWorkspace& ws, const Prepared& P, int R, const TileSh
     ov.rec_row = step;
     ov.spin_limit = P.spin_limit;
     ov.debug_skip_plane = -1;
-    for (int j = 0; j <= kMaxR; ++j) ov.c[j] = P.c[j];
+    for (int j = 0; j < kMaxR + 2; ++j) ov.c[j] = P.c[j];
     if (P.waves) {
       const char* base = static_cast<const char*>(ws.desc.p);
       ov.item_start = reinterpret_cast<const int32_t*>(base + P.off_start);

@@ -50,16 +50,18 @@ struct Box {
   float* A = nullptr;
   CUtensorMap mapA;
   Tables tab;
-  float* msg[27] = {};  // message buffers towards the neighbours, by direction
-  int nb[27];            // neighbour box per direction (-1: none)
+  float* msg[6] = {};  // face messages x-, x+, y-, y+, z-, z+ (faces with a neighbour)
+  int nb[27];           // neighbour box per direction (dx+1) + 3(dy+1) + 9(dz+1), -1: none
 };
 
-// One unpack block: a contiguous message [n2][n1][n0] copied into a strided
-// region of the receiving box's wavefield (buffer selected per step).
+// One unpack block of n0 x n1 x n2 points: from a face message (row stride
+// r1, plane stride r2 within it: the whole message or a sub-block of it) into
+// a strided region of the receiving box's wavefield (buffer chosen per step).
 struct Msg {
   const float* src;
   float* dst[2];
   int n0, n1, n2;
+  int r1, r2;        // source strides (floats)
   int s1;            // destination row pitch (floats)
   long long s2;      // destination plane stride (floats)
 };
@@ -89,7 +91,7 @@ __global__ void k_unpack(const Msg* __restrict__ msgs, int nb) {
   for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < rows; r += gridDim.x * blockDim.y) {
     const int i1 = r % m.n1, i2 = r / m.n1;
     float* d = dst + i2 * m.s2 + static_cast<long long>(i1) * m.s1;
-    const float* sp = m.src + static_cast<long long>(r) * m.n0;
+    const float* sp = m.src + static_cast<long long>(i2) * m.r2 + static_cast<long long>(i1) * m.r1;
     for (int i0 = threadIdx.x; i0 < m.n0; i0 += blockDim.x) d[i0] = sp[i0];
   }
 }
@@ -112,7 +114,7 @@ void release(fd_grid g, Cart* c) {
     for (int k = 0; k < 2; ++k)
       if (b.F.u[k]) cudaFree(b.F.u[k]);
     if (b.A) cudaFree(b.A);
-    for (int f = 0; f < 27; ++f)
+    for (int f = 0; f < 6; ++f)
       if (b.msg[f]) cudaFree(b.msg[f]);
     for (DevBuf* d : {&b.tab.inj_start, &b.tab.inj, &b.tab.rec_start, &b.tab.recs}) d->release();
   }
@@ -296,10 +298,14 @@ fd_status gather(fd_grid g, Cart* c) {
   return FD_OK;
 }
 
-// Unpack list: box b's ghost block towards direction d receives the
-// neighbour's message of the opposite direction (-d): along an axis with
-// d = 0 the owned range, with d = -1 the R ghost layers below the first owned
-// one, with d = +1 the R above the last.
+// Unpack list: box b's ghost block towards direction d is the neighbour n
+// = b + d's owned block next to b: along an axis with d = 0 the owned range,
+// with d = -1 the R layers below b's first owned one (n's last R), with d = +1
+// the R above b's last (n's first R).  That block lies in one of n's face
+// messages, the one of the first axis a with d_a != 0 (n's face towards b on
+// that axis, f = 2a + (d_a < 0)): the whole message for a face neighbour, a
+// sub-block of it (the first or last R rows or planes of the other axes) for
+// an edge or corner neighbour.
 fd_status build_messages(fd_grid g, Cart* c) {
   const int R = g->R;
   const int first[3] = {c->gx, R, R};
@@ -310,13 +316,22 @@ fd_status build_messages(fd_grid g, Cart* c) {
       if (k == 13 || b.nb[k] < 0) continue;
       const int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
       const Box& n = c->box[b.nb[k]];
-      Msg m;
-      m.src = n.msg[26 - k];  // direction -d
-      int o[3], e[3];
+      int ax = 0;
+      while (d[ax] == 0) ++ax;
+      const int f = 2 * ax + (d[ax] < 0 ? 1 : 0);  // n's face towards b
+      // extents of the face message of n along x, y, z, and the first point
+      // of the block within it
+      int me[3], mo[3], e[3], o[3];
       for (int a = 0; a < 3; ++a) {
+        me[a] = a == ax ? R : n.on[a];
         e[a] = d[a] ? R : b.on[a];
+        mo[a] = (a == ax || d[a] >= 0) ? 0 : n.on[a] - R;  // d = -1: n's last R
         o[a] = d[a] == 0 ? first[a] : (d[a] > 0 ? first[a] + b.on[a] : first[a] - R);
       }
+      Msg m;
+      m.src = n.msg[f] + ((long long)mo[2] * me[1] + mo[1]) * me[0] + mo[0];
+      m.r1 = me[0];
+      m.r2 = me[0] * me[1];
       m.n0 = e[0];
       m.n1 = e[1];
       m.n2 = e[2];
@@ -414,7 +429,7 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
     a.offx = off_x(c, b);
     a.offy = off_y(g, b);
     a.offz = off_z(g, b);
-    for (int f = 0; f < 27; ++f) a.pack[f] = b.nb[f] >= 0 ? b.msg[f] : nullptr;
+    for (int f = 0; f < 6; ++f) a.pack[f] = b.msg[f];
     a.onx = b.on[0];
     a.ony = b.on[1];
     a.onz = b.on[2];
@@ -469,7 +484,7 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
       ov.rec_row = t;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = -1;
-      for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= R ? float(g->c[j]) : 0.0f;
+      launch_weights(g->c, R, ov.c);
       cudaError_t e2 = launch_sweep(R, g->shape, kModePack, sd, pf, nbox, ov, ctas, s);
       if (!e2 && c->nmsg > 0) {
         count_launch();
@@ -592,12 +607,14 @@ extern "C" fd_status fd_set_topology(fd_grid g, int32_t px, int32_t py, int32_t 
           if (!e) e = cudaMemsetAsync(b.A, 0, b.ncell * 4, g->stream);
           if (e) st = cuda_fail(e, "box model allocation");
         }
-        for (int f = 0; f < 27 && !st; ++f) {
-          if (b.nb[f] < 0) continue;
-          size_t n = 1;
-          for (int a = 0; a < 3; ++a) n *= size_t((f / (a == 0 ? 1 : a == 1 ? 3 : 9)) % 3 == 1
-                                                      ? b.on[a]
-                                                      : R);
+        // face messages: face f (axis f / 2, low side for even f) towards the
+        // neighbour in direction index 13 -/+ 1, 3, 9
+        for (int f = 0; f < 6 && !st; ++f) {
+          const int step = f < 2 ? 1 : f < 4 ? 3 : 9;
+          if (b.nb[13 + (f & 1 ? step : -step)] < 0) continue;
+          size_t n = R;
+          for (int a = 0; a < 3; ++a)
+            if (a != f / 2) n *= size_t(b.on[a]);
           e = dev_alloc(reinterpret_cast<void**>(&b.msg[f]), n * 4);
           if (e) st = cuda_fail(e, "message buffer allocation");
         }

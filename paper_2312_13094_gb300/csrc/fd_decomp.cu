@@ -343,7 +343,7 @@ fd_status decomp_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
       ov.rec_row = t;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = -1;
-      for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= R ? float(g->c[j]) : 0.0f;
+      launch_weights(g->c, R, ov.c);
       const ShotDesc* sd = reinterpret_cast<const ShotDesc*>(base + i * kBlock);
       const long long* pf = reinterpret_cast<const long long*>(base + i * kBlock + sizeof(ShotDesc));
       return launch_sweep(R, g->shape, mode, sd, pf, 1, ov, ctas[i], s);

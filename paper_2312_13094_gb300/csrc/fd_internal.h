@@ -75,13 +75,11 @@ struct StepArgs {
   // array coordinate plus (offx, offy, offz), which places the damping layer.
   int32_t xfirst, yfirst, xend, yend;
   int32_t offx, offy, offz;
-  // kModePack: message buffers towards the 26 neighbours, direction
-  // (dx, dy, dz) in {-1, 0, 1}^3 at index (dx+1) + 3 (dy+1) + 9 (dz+1)
-  // (nullptr: no neighbour there), and the owned extents.  A message holds
-  // the owned points next to that neighbour: along an axis with d = 0 the
-  // whole owned range, with d = -1 the first R layers, with d = +1 the last R,
-  // stored [z][y][x] over that block.
-  float* pack[27];
+  // kModePack: message buffers of the faces x-, x+, y-, y+, z-, z+ (nullptr:
+  // no neighbour there) and the owned extents; face f holds the R owned
+  // layers next to it, [z][y][j] for the x faces, [z][j][x] for y, [j][y][x]
+  // for z (j counted from the face's low side).
+  float* pack[6];
   int32_t onx, ony, onz;
 };
 
@@ -115,7 +113,10 @@ struct StepOverride {
   float* e_out;
   const float* e_in;
   long long spin_limit;      // clock cycles before a wait gives up
-  float c[kMaxR + 1];        // stencil weights shared by every shot of the launch
+  float c[kMaxR + 2];        // stencil weights shared by every shot of the launch:
+                             // c[0] the centre weight -6 sum c_j (hi part, see
+                             // launch_weights), c[1..R] the weights c_j, c[kMaxR+1] the
+                             // centre weight's lo part
   const int32_t* item_start; // scheduled sweep: CTA c runs items [item_start[c],
   const WorkItem* items;     // item_start[c+1]); nullptr: equal contiguous shares
 };
@@ -158,10 +159,26 @@ struct TbLaunch {
   int in_prev, in_cur, out1, out2;
   int inj_row, rec_row;
   long long spin_limit;
-  float c[kMaxR + 1];
+  float c[kMaxR + 2];  // as StepOverride::c
   const int32_t* item_start;
   const WorkItem* items;
 };
+
+// The weights of a uniform-stencil launch from the FP64 weights c[0..R]
+// (host side): out[j] = c_j rounded to FP32 for j = 1..R, and the centre
+// weight T = -6 sum_j out[j] (exact in FP64) as out[0] + out[kMaxR+1], the
+// FP32 hi and lo parts; zero beyond R.
+inline void launch_weights(const double* c, int R, float* out) {
+  double t = 0.0;
+  for (int j = 0; j < kMaxR + 2; ++j) out[j] = 0.0f;
+  for (int j = 1; j <= R; ++j) {
+    out[j] = static_cast<float>(c[j]);
+    t += static_cast<double>(out[j]);
+  }
+  t *= -6.0;
+  out[0] = static_cast<float>(t);
+  out[kMaxR + 1] = static_cast<float>(t - static_cast<double>(out[0]));
+}
 
 struct TileShape {
   int tx, ty, pf;   // threads in x (4 points each), rows, prefetch depth

@@ -763,7 +763,7 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
   key.sched = sched_ov.items;
   key.skip = g->debug_skip_plane;
   key.spin = g->spin_limit;
-  for (int j = 0; j <= kMaxR; ++j) key.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
+  launch_weights(g->c, g->R, key.c);
   const bool reuse = use_graph && g->graph_valid && memcmp(&key, &g->gkey, sizeof(key)) == 0;
   if (g->profiling) cudaEventRecord(g->ev0, g->stream);
   const int cur0 = F.cur;
@@ -787,7 +787,7 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
       ov.items = sched_ov.items;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = (t == 0) ? g->debug_skip_plane : -1;
-      for (int j = 0; j <= kMaxR; ++j) ov.c[j] = j <= g->R ? float(g->c[j]) : 0.0f;
+      launch_weights(g->c, g->R, ov.c);
       ov.inj_row = rs.inj_row0 + rs.inj_row_step * t;
       ov.rec_row = rs.rec_row0 + rs.rec_row_step * t;
       if (mode == kModeStoreE) ov.e_out = rs.e_base + size_t(t) * g->ncell;

@@ -64,7 +64,7 @@ struct GraphKey {
   const void* sched;  // work items of a wave-scheduled sweep (nullptr: equal shares)
   int skip;
   long long spin;
-  float c[kMaxR + 1];
+  float c[kMaxR + 2];
 };
 
 struct Decomp;  // domain decomposition state of a grid (fd_decomp.cu)

@@ -185,27 +185,15 @@ __device__ __forceinline__ float2 half2of(const float4& v, int p) {
   return p == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
 }
 
-// Centre weight of the uniform stencil, -6 sum_{j>=1} c_j for the FP32
-// weights c_j, as an FP32 pair hi + lo (the sum is exact in FP64, and hi + lo
-// holds it to ~1e-15).  With hi alone the rounded centre weight leaves the
-// stencil a row sum of ~1e-7: the Laplacian of a constant field is then not
-// zero but that constant times a fixed bias, a spurious mass term whose phase
-// error grows with every step (about 1e-5 of the wavefield after 200 steps
-// at space order 8).  With the pair the residual is rounding noise without a
-// bias.
-template <int R>
-__device__ __forceinline__ void centre_weight(const float* c, float& hi, float& lo) {
-  double t = 0.0;
-#pragma unroll
-  for (int j = 1; j <= R; ++j) t += static_cast<double>(c[j]);
-  t *= -6.0;
-  hi = static_cast<float>(t);
-  lo = static_cast<float>(t - static_cast<double>(hi));
-}
-
 // h^2 times the Laplacian of four consecutive x points with uniform weights:
 // lap = (hi + lo) u + sum_{j=1..R} c_j S_j, S_j the sum of the six neighbours
-// at distance j (centre_weight gives hi, lo).  Lanes (0,1) and (2,3) run as
+// at distance j, hi + lo = -6 sum c_j the centre weight of the FP32 weights c_j
+// (launch_weights: exact in FP64, split into FP32 hi and lo parts).  With hi
+// alone the rounded centre weight leaves the stencil a row sum of ~1e-7: the
+// Laplacian of a constant field is then not zero but that constant times a
+// fixed bias, a spurious mass term whose phase error grows with every step
+// (about 1e-5 of the wavefield after 200 steps at space order 8).  With the
+// pair the residual is rounding noise without a bias.  Lanes (0,1) and (2,3) run as
 // packed pairs: each packed operation rounds every lane exactly as its scalar
 // form.  xr holds the row through the points (the points at xr[XO .. XO+3]),
 // yn(j, lo, hi) gives the float4s j rows below and above, zn(o) the float4 of
@@ -292,40 +280,28 @@ __device__ __forceinline__ void update4_layer(const float lap[4], const float sr
 }
 
 // kModePack epilogue: the updated values of four owned points (owned
-// coordinates ox..ox+3, oy, oz) that lie within R layers of the box's faces
-// also go to the message of every neighbour they border: the face
-// neighbours, and the edge and corner neighbours where two or three faces
-// meet (the star stencil reads only faces, trilinear receivers near an edge
-// of the box also read edge and corner ghosts).
+// coordinates ox..ox+3, oy, oz) within R layers of a face with a neighbour
+// also go to that face's message.  Faces only: the edge and corner ghosts of
+// a box are filled from sub-blocks of its diagonal neighbours' face messages,
+// which hold those points too.  zlo / zhi: oz is within R of the z faces.
 template <int R>
 __device__ __forceinline__ void pack_faces(const StepArgs& a, const float res[4], int ox, int oy,
-                                           int oz) {
-  const bool ylo = oy < R, yhi = oy >= a.ony - R, zlo = oz < R, zhi = oz >= a.onz - R;
-  if (!(ox < R || ox + 3 >= a.onx - R || ylo || yhi || zlo || zhi)) return;
+                                           int oz, bool zlo, bool zhi) {
+  const bool ylo = oy < R, yhi = oy >= a.ony - R;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
     const int x = ox + l;
     if (x >= a.onx) break;
-    const bool xlo = x < R, xhi = x >= a.onx - R;
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-      if ((dz < 0 && !zlo) || (dz > 0 && !zhi)) continue;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        if ((dy < 0 && !ylo) || (dy > 0 && !yhi)) continue;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          if ((dx < 0 && !xlo) || (dx > 0 && !xhi) || (dx == 0 && dy == 0 && dz == 0)) continue;
-          float* p = a.pack[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
-          if (!p) continue;
-          const int ex = dx ? R : a.onx, ey = dy ? R : a.ony;
-          const int ix = dx > 0 ? x - (a.onx - R) : x;
-          const int iy = dy > 0 ? oy - (a.ony - R) : oy;
-          const int iz = dz > 0 ? oz - (a.onz - R) : oz;
-          p[(static_cast<size_t>(iz) * ey + iy) * ex + ix] = res[l];
-        }
-      }
-    }
+    const float v = res[l];
+    if (x < R && a.pack[0]) a.pack[0][(static_cast<size_t>(oz) * a.ony + oy) * R + x] = v;
+    if (x >= a.onx - R && a.pack[1])
+      a.pack[1][(static_cast<size_t>(oz) * a.ony + oy) * R + (x - (a.onx - R))] = v;
+    if (ylo && a.pack[2]) a.pack[2][(static_cast<size_t>(oz) * R + oy) * a.onx + x] = v;
+    if (yhi && a.pack[3])
+      a.pack[3][(static_cast<size_t>(oz) * R + (oy - (a.ony - R))) * a.onx + x] = v;
+    if (zlo && a.pack[4]) a.pack[4][(static_cast<size_t>(oz) * a.ony + oy) * a.onx + x] = v;
+    if (zhi && a.pack[5])
+      a.pack[5][(static_cast<size_t>(oz - (a.onz - R)) * a.ony + oy) * a.onx + x] = v;
   }
 }
 
@@ -356,7 +332,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            unsigned char* smem) {
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
-  constexpr int NQ = 2 * R + 1;
+  // z neighbours: the wide stencils (R >= 5) keep only planes k-R .. k in the
+  // register queue and read the planes above from the ring, which holds them
+  // anyway (halving the queue's registers and its shift); the others keep all
+  // 2R+1 planes in registers
+  constexpr bool HALFQ = R >= 5;
+  constexpr int NQ = HALFQ ? R + 1 : 2 * R + 1;
   constexpr uint32_t URING = C::SU * C::UPITCH;
   constexpr uint32_t ARING = C::SA * C::TPITCH;
   const int tid = threadIdx.x;
@@ -442,7 +423,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   for (int j = 0; j < 2 * R; ++j) {
     const int slot = j % C::SU;
     bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, ov.spin_limit);
-    q[j] = *reinterpret_cast<const float4*>(ubuf + slot * C::UPITCH + crow);
+    if (!HALFQ || j < R) q[j] = *reinterpret_cast<const float4*>(ubuf + slot * C::UPITCH + crow);
     if (j < R) {
       if (__syncthreads_or(bad)) goto fail;
       if (tid == 0) issue_u(j + C::SU, slot * C::UPITCH);
@@ -471,8 +452,11 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx;
     const bool in_grid = gy < a.yend && gx < a.xend;
-    float c0hi = 0.f, c0lo = 0.f;
-    centre_weight<R>(ov.c, c0hi, c0lo);
+    // kModePack: the thread's points lie within R columns or rows of a face
+    const bool xy_edge = MODE == kModePack &&
+                         (gx - a.xfirst < R || gx - a.xfirst + 3 >= a.onx - R ||
+                          gy - a.yfirst < R || gy - a.yfirst >= a.ony - R);
+    const float c0hi = ov.c[0], c0lo = ov.c[kMaxR + 1];  // centre weight (launch_weights)
     // the layer in array coordinates (shifted for subdomains)
     const int nblx = a.nbl - a.offx, nbly = a.nbl - a.offy, nblz = ov.nblz - a.offz;
     const int dyv = sponge_depth(gy, nbly, a.ny);
@@ -509,14 +493,29 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     int sa = 0;
     uint32_t pa = 0;
 
+    // up to SO 8 two planes per loop trip: the compiler renames the queue for
+    // the first of them instead of shifting it (measured +2 % on 592^3 SO 8;
+    // the wider stencils would spill)
+    constexpr int kUnroll = R <= 4 ? 2 : 1;
+#pragma unroll kUnroll
     for (int k = zbeg; k < zend; ++k) {
       {
 #define FD_Q(o) q[R + (o)]
         const int ik = k - zbeg;
         const int jk = ik + R;
         bad |= !mbar_wait(bar_u0 + 8 * sn, pn, ov.spin_limit);
-        FD_Q(R) = *reinterpret_cast<const float4*>(ubuf + sn * C::UPITCH + crow);
+        if (HALFQ)
+          FD_Q(0) = *reinterpret_cast<const float4*>(ubuf + sk * C::UPITCH + crow);
+        else
+          q[2 * R] = *reinterpret_cast<const float4*>(ubuf + sn * C::UPITCH + crow);
         bad |= !mbar_wait(bar_a0 + 8 * sa, pa, ov.spin_limit);
+        // the float4 of the plane at z offset o (-R .. R): register queue, or
+        // for o > 0 with the half queue the ring slot holding it
+        auto zq = [&](int o) -> float4 {
+          if (!HALFQ || o <= 0) return q[R + o];
+          const int sl = sk + o >= C::SU ? sk + o - C::SU : sk + o;
+          return *reinterpret_cast<const float4*>(ubuf + sl * C::UPITCH + crow);
+        };
 
         const unsigned char* P = ubuf + sk * C::UPITCH + crow;
         float xr[4 * C::NROW4];
@@ -565,7 +564,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             for (int l = 0; l < 4; ++l) {
               const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
               const float sy = lane(ym, l) + lane(yp, l);
-              const float sz = lane(FD_Q(-jj), l) + lane(FD_Q(jj), l);
+              const float sz = lane(zq(-jj), l) + lane(zq(jj), l);
               const float cj = (MODE == kModeTable) ? ct[l][jj - 1] : lane(cv, l);
               const float d = fmaf(-6.0f, xr[C::RX + l], (sx + sy) + sz);
               lap[l] = (jj == 1) ? cj * d : fmaf(cj, d, lap[l]);
@@ -578,7 +577,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
                 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
               },
-              [&](int o) { return FD_Q(o); }, ov.c, c0hi, c0lo, lap);
+              zq, ov.c, c0hi, c0lo, lap);
         }
 
         // point sources of this plane (owner thread adds its share)
@@ -626,7 +625,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             g.w -= uc.w * ein.w * a.inv_dt2;
             *reinterpret_cast<float4*>(a.grad + off) = g;
           }
-          if (MODE == kModePack) pack_faces<R>(a, res, gx - a.xfirst, gy - a.yfirst, k - ov.zfirst);
+          if (MODE == kModePack) {
+            const int oz = k - ov.zfirst;
+            const bool zlo = oz < R, zhi = oz >= a.onz - R;
+            if (xy_edge || zlo || zhi)
+              pack_faces<R>(a, res, gx - a.xfirst, gy - a.yfirst, oz, zlo, zhi);
+          }
         }
         off += plane_stride;
 
@@ -662,7 +666,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         sa = (sa + 1 == C::SA) ? 0 : sa + 1;
         pa ^= (sa == 0) ? 1u : 0u;
 #pragma unroll
-        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+        for (int j = 0; j < NQ - 1; ++j) q[j] = q[j + 1];
 #undef FD_Q
       }
     }

@@ -156,7 +156,7 @@ fd_status tblock_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
   TbLaunch L;
   memset(&L, 0, sizeof(L));
   L.spin_limit = g->spin_limit;
-  for (int j = 0; j <= kMaxR; ++j) L.c[j] = j <= R ? float(g->c[j]) : 0.0f;
+  launch_weights(g->c, R, L.c);
   L.item_start = static_cast<const int32_t*>(t->sched.p);
   L.items = reinterpret_cast<const WorkItem*>(static_cast<const char*>(t->sched.p) +
                                               t->sched_off);

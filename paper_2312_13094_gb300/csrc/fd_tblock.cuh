@@ -194,8 +194,7 @@ __device__ __forceinline__ void tb_column(const TbDesc* __restrict__ D, const Tb
     xy_inner = xy_inner && dyv == 0;  // inside the physical box in x and y: b = 0
     const size_t plane_stride = static_cast<size_t>(a.Ny) * a.pitch;
     const size_t col = static_cast<size_t>(gy) * a.pitch + gx;
-    float c0hi = 0.f, c0lo = 0.f;
-    centre_weight<R>(L.c, c0hi, c0lo);
+    const float c0hi = L.c[0], c0lo = L.c[kMaxR + 1];  // centre weight (launch_weights)
     float* out1 = D->u[L.out1];
     float* out2 = D->u[L.out2];
 

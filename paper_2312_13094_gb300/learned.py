@@ -246,6 +246,77 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+_FINE_CACHE = {}
+
+
+def fine_receivers(seed, device=0, timed=True, **kw):
+    """Receivers (and GPU time) of the fine SO 16 solve of one model (`kw` as
+    for pair), kept for the process so that evaluations and the fine-tune
+    share them."""
+    key = (seed, tuple(sorted(kw.items())))
+    if key not in _FINE_CACHE:
+        fine, _ = pair(seed, **kw)
+        _FINE_CACHE[key] = run_forward(fine, device, timed=timed)
+    return _FINE_CACHE[key]
+
+
+# the output-layer bias of the network: entries o_j and o_{j+4} of the 8
+# outputs enter weight j only through their mean, so 4 directions matter
+_B3 = 5000 - 8
+
+
+def finetune_output_bias(net, seeds, device=0, iters=12, h0=0.05, table=256, **kw):
+    """Rollout fine-tune of the network's output bias on the receiver misfit.
+
+    The one-step training sets the weights from local fine-run samples; the
+    quantity they are judged by is the receiver error of whole coarse runs.
+    This stage moves the bias of output pair j (o_j, o_{j+4}) by beta_j to
+    minimise the largest receiver relative L2, against the fine solve, over
+    the training models `seeds`: each iteration estimates the gradient of
+    that objective by central differences (step h) through coarse forward
+    runs of the library and takes a backtracking step (`kw` as for pair).
+    Returns the history of the objective and the bias shifts."""
+    p0 = net.params().astype(np.float64)
+    refs = {s: fine_receivers(s, device=device, **kw)[0][::2] for s in seeds}
+    coarse = {s: pair(s, **kw)[1] for s in seeds}
+
+    def objective(beta):
+        p = p0.copy()
+        for j in range(4):
+            p[_B3 + j] += beta[j]
+            p[_B3 + 4 + j] += beta[j]
+        net.set_params(p.astype(np.float32))
+        return max(rel_l2(run_forward(coarse[s], device, net=net.handle, table=table,
+                                      timed=False)[0], refs[s]) for s in seeds)
+
+    beta = np.zeros(4)
+    f = objective(beta)
+    hist = [f]
+    h = h0
+    for _ in range(iters):
+        g = np.zeros(4)
+        for j in range(4):
+            e = np.zeros(4)
+            e[j] = h
+            g[j] = (objective(beta + e) - objective(beta - e)) / (2 * h)
+        if not np.any(g):
+            break
+        step = 4 * h / np.abs(g).max()
+        improved = False
+        for _ in range(5):
+            trial = beta - step * g
+            ft = objective(trial)
+            if ft < f:
+                beta, f, improved = trial, ft, True
+                break
+            step *= 0.5
+        hist.append(f)
+        if not improved:
+            h *= 0.5
+    objective(beta)  # leave the network at the best bias
+    return hist, beta
+
+
 def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True, ladder=False):
     """Per held-out model: receiver rel. L2 of coarse plain and coarse learned
     against the fine SO 16 solve (fine rec[2k]), and the GPU times; with
@@ -253,7 +324,7 @@ def evaluate(net, seeds, n=512, nt=1250, device=0, timed=True, ladder=False):
     rows = []
     for s in seeds:
         fine, coarse = pair(s, n=n, nt=nt)
-        rf, tf = run_forward(fine, device, timed=timed)
+        rf, tf = fine_receivers(s, device=device, timed=timed, n=n, nt=nt)
         ref = rf[::2]
         extra = {}
         if ladder:

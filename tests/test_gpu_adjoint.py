@@ -182,4 +182,4 @@ def test_directional_derivative_on_the_configured_grid(fd):
     gap = abs(fd_dir - ad_dir) / abs(ad_dir)
     print(f"296^3 x 500, 25 checkpoints: <g, dm> {ad_dir:.6e}, central difference "
           f"{fd_dir:.6e}, relative gap {gap:.2e}")
-    assert gap <= 2e-3, (fd_dir, ad_dir)
+    assert gap <= 1e-4, (fd_dir, ad_dir)  # measured 1.0e-5 on GB300
