@@ -513,11 +513,15 @@ def run_batched(args):
 
 def run_decomposed(args):
     """The headline grid cut into z slabs (fd_set_decomposition) in both
-    exchange modes and into Cartesian boxes (fd_set_topology: the six face
-    messages packed in the step's epilogue, one unpack kernel per step),
-    against the same grid undecomposed: Gpts/s of whole fd_forward runs
-    (device time, CUDA events), so the difference is what the ghost layers,
-    the messages and the extra launches cost on one GPU."""
+    exchange modes and into Cartesian boxes (fd_set_topology: after every
+    step a pack kernel copies the faces into six messages and an unpack kernel
+    fills the ghost layers), against the same grid undecomposed: Gpts/s of
+    whole fd_forward runs (device time, CUDA events), so the difference is
+    what the ghost layers, the messages and the extra launches cost on one
+    GPU.  Two schedules: equal shares on the default tile (slabs, boxes and
+    the whole grid alike) and column waves on the 64 x 16 tile (boxes and the
+    whole grid); each row is compared with the whole grid on its own
+    schedule."""
     import torch
     from paper_2312_13094_gb300 import binding as fd
     from paper_2312_13094_gb300 import workloads as wl
@@ -529,17 +533,21 @@ def run_decomposed(args):
     peak, kind = _peaks()
     with torch.cuda.stream(stream):
         g = fd.Grid.from_workload(w, stream=stream.cuda_stream)
-        # slabs run the default tile with equal shares: keep the whole grid
-        # on the same (no tuning), so the rows differ only by the slabs
+        # no tuning: every row names its tile and schedule
         i0 = g.info()
-        g.set_tile(i0["tile_x"], i0["tile_y"], 0)
+        shares = (i0["tile_x"], i0["tile_y"], fd.FD_SCHED_SHARES)
+        waves = (64, 16, fd.FD_SCHED_WAVES)
         v_dev = torch.from_numpy(w["v"]).cuda()
         wav = torch.from_numpy(np.ascontiguousarray(w["wavelet"])).cuda()
         rec = torch.zeros((nt, len(w["rec"])), device="cuda")
         ref = None
-        cases = [(1, 0, None)] + [(p, m, None) for p in args.slabs for m in (0, 1)]
-        cases += [(1, 0, t) for t in args.topos]
-        for nsub, mode, topo in cases:
+        cases = [(1, 0, None, shares)] + [(p, m, None, shares) for p in args.slabs
+                                           for m in (0, 1)]
+        cases += [(1, 0, t, shares) for t in args.topos]
+        cases += [(1, 0, None, waves)] + [(1, 0, t, waves) for t in args.topos]
+        for nsub, mode, topo, (tx, ty, sched) in cases:
+            g.set_tile(tx, ty, 0)
+            g.set_schedule(sched)
             if topo is None:
                 g.set_topology(1, 1, 1)
                 g.set_decomposition(nsub, mode)
@@ -562,23 +570,25 @@ def run_decomposed(args):
             else:
                 same = bool(torch.equal(rec, ref))
             gpts = npts * nt / (ms * 1e-3) / 1e9
-            row = {"slabs": nsub, "mode": ["basic", "overlap"][mode], "ms": ms,
-                   "gpts": gpts, "frac": 16 * gpts / peak,
+            row = {"slabs": nsub, "mode": ["basic", "overlap"][mode],
+                   "schedule": "waves" if sched == fd.FD_SCHED_WAVES else "shares",
+                   "tile": [tx, ty], "ms": ms, "gpts": gpts, "frac": 16 * gpts / peak,
                    "launches_per_run": int(launches), "receivers_bitwise_equal": same}
             if topo is not None:
                 row.update({"slabs": None, "topology": "x".join(map(str, topo)),
-                            "mode": "basic, boxes with the pack fused into the step"})
+                            "mode": "boxes: step, pack kernel, unpack kernel"})
             rows.append(row)
         g.set_decomposition(1)
         g.set_topology(1, 1, 1)
         g.close()
-    base = rows[0]["gpts"]
+    base = {r["schedule"]: r["gpts"] for r in rows
+            if r["slabs"] == 1 and "topology" not in r}
     for r in rows:
-        r["vs_undecomposed"] = r["gpts"] / base
+        r["vs_undecomposed"] = r["gpts"] / base[r["schedule"]]
     print(json.dumps({"metric": "Gpts/s", "unit": "Gpts/s", "higher_is_better": True,
                       "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
                       "data": "synthetic", "peak": peak, "peak_kind": kind,
-                      "config": {"workload": w["name"] + " in z slabs",
+                      "config": {"workload": w["name"] + " in z slabs and boxes",
                                  "grid_padded": _padded(w), "nt": nt},
                       "rows": rows}), flush=True)
 

@@ -214,13 +214,13 @@ fd_status fd_set_decomposition(fd_grid grid, int32_t nsub, int32_t mode);
  * fastest, keeps its two wavefields and model term with ghost layers (R
  * rounded up to four floats in x, R in y and z), and every later
  * fd_forward / fd_propagate on this grid steps all boxes in one launch per
- * step.  The step writes, besides u^{n+1}, the updated points within R
- * layers of each cut into the contiguous message of every neighbour they
- * border (the pack is fused into the step); one unpack kernel then copies
- * every message into the receiver's ghost block.  One message per face,
- * edge and corner neighbour (the paper's diagonal mode: up to 26 per box):
- * the stencil reads the faces, receivers next to an edge of a box also read
- * edge and corner ghosts.  Every point is computed exactly as in the
+ * step (column waves over the boxes one after another; equal shares under
+ * FD_SCHED_SHARES or an explicit CTA count).  After the step a pack kernel copies the R updated layers next to
+ * each face with a neighbour into that face's contiguous message, and an
+ * unpack kernel fills every ghost block from them: faces from the face
+ * neighbour's message, edges and corners (read by receivers next to two or
+ * three cuts; the stencil reads faces only) from sub-blocks of the diagonal
+ * neighbour's face messages.  Every point is computed exactly as in the
  * undecomposed run (receivers and wavefields equal bit for bit); the
  * whole-grid state is scattered before a run and gathered after it.  All
  * boxes live on the grid's device; across GPUs each message would be one
@@ -295,9 +295,12 @@ fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas
  *                    odd step count ends with one single step.  Other space
  *                    orders, per-cell or table weights and decomposed grids
  *                    run single steps with equal shares instead.
- * Adjoint and per-cell/table-weight steps always use equal shares on the
- * default tile; an explicit CTA count (fd_set_tile ctas > 0) uses equal
- * shares too.  Every schedule and tile gives the same results bit for bit.
+ * The adjoint's steps (fd_adjoint, fd_gradient) and table-weight forward
+ * steps follow the same choice as plain forward runs (the tuner's tile and
+ * schedule once the grid has been tuned); per-cell weight fields always use
+ * equal shares on the default tile, and so does an explicit CTA count
+ * (fd_set_tile ctas > 0).  Every schedule and tile gives the same results
+ * bit for bit.
  * Errors: FD_ERR_ARG (unknown mode). */
 enum { FD_SCHED_AUTO = 0, FD_SCHED_SHARES = 1, FD_SCHED_WAVES = 2, FD_SCHED_TEMPORAL = 3 };
 fd_status fd_set_schedule(fd_grid grid, int32_t mode);

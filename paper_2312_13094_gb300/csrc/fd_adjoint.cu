@@ -49,9 +49,10 @@ fd_status adjoint_impl(fd_grid g, const fd_points* src, const float* wavelet,
                        const fd_points* rec, const float* d_obs, const float* resid_in,
                        int32_t n_checkpoints, float* grad_m, double* loss_out) {
   {
-    // the adjoint's launches run on the base tile, whatever the tuner picked
-    // for plain forward runs
-    fd_status st0 = use_shape(g, false);
+    // the adjoint's launches (recompute and adjoint modes) take the tuner's
+    // pick of tile and schedule for the grid's size, as plain forward runs do
+    // (every tile and schedule gives the same bits)
+    fd_status st0 = use_shape(g, true);
     if (st0) return st0;
   }
   if (!g->model_set) return fail(FD_ERR_STATE, "fd_set_model has not been called");
@@ -70,6 +71,17 @@ fd_status adjoint_impl(fd_grid g, const fd_points* src, const float* wavelet,
   cudaError_t e;
   fd_status st;
 
+  // a grid left on the default tile is tuned by its first long run, whether
+  // that is a forward run or this one (source-free steps on zeroed
+  // wavefields), before the point tables are built for the tile in use
+  if (g->auto_tile && !g->tuned && g->sched_mode == FD_SCHED_AUTO && !g->dmp && !g->cart &&
+      nt >= kTuneMinSteps && g->debug_skip_plane < 0) {
+    for (int b = 0; b < 2; ++b)
+      if ((e = cudaMemsetAsync(g->F.u[b], 0, cell_bytes, g->stream)))
+        return cuda_fail(e, "wavefield reset");
+    g->F.cur = 0;
+    if ((st = autotune_grid(g))) return st;
+  }
   if ((st = ensure_adjoint_fields(g))) return st;
   if ((e = g->ckpt.ensure(std::max<size_t>(size_t(std::max(nseg - 1, 0)) * 2 * cell_bytes, 16))))
     return cuda_fail(e, "checkpoint allocation");

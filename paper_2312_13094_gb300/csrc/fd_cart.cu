@@ -7,10 +7,12 @@
 // and unpacks what it receives into its halo.  Its "basic" mode fills edges
 // and corners of the halo by exchanging axis after axis; its "diagonal" mode
 // sends one message per neighbour, faces, edges and corners (26 in 3-D), in
-// a single exchange.  Here every message can only hold owned values, written
-// while the step stores them, so the exchange is the diagonal one.  The star
-// stencil itself reads only the six faces; the edge and corner ghosts serve
-// the trilinear receivers whose eight nodes straddle two or three cuts.
+// a single exchange.  Here six face messages of owned values are packed and
+// every ghost block, faces, edges and corners, is filled from them in one
+// exchange (an edge or corner block is part of a diagonal neighbour's face
+// message).  The star stencil itself reads only the six faces; the edge and
+// corner ghosts serve the trilinear receivers whose eight nodes straddle two
+// or three cuts.
 //
 // Layout.  Box b owns the padded ranges [gx0, gx0 + onx) x [gy0, gy0 + ony)
 // x [gz0, gz0 + onz) (per axis the balanced split of the padded extent) and
@@ -19,18 +21,22 @@
 // floats so that every tile's TMA x coordinate stays 16-byte aligned.  Ghost
 // layers beyond the grid are zero and never written.
 //
-// Step.  One launch of the sweep kernel in kModePack steps every box (the
-// boxes are the "shots" of the launch, with their own tensor maps, tables
-// and array offsets that keep the damping layer in global coordinates).
-// While a point's u^{n+1} is stored, the ones within R layers of a cut are
-// written to the contiguous message of every neighbour they border as well:
-// the pack is fused into the step's epilogue.  One unpack kernel then copies
-// every message into the receiving box's ghost block of the buffer the step
-// wrote.  On one GPU the unpack reads the sender's message buffer directly;
-// across GPUs a peer copy (or NCCL send/recv) of each contiguous message into
-// the receiver's memory would come in between.  Every point goes through the
-// same arithmetic as in the undecomposed run, so both give the same
-// wavefields and receivers bit for bit.
+// Step.  One launch of the plain sweep kernel steps every box (the boxes are
+// the "shots" of the launch, with their own tensor maps, tables and array
+// offsets that keep the damping layer in global coordinates).  A pack kernel
+// then copies the R updated layers next to each face with a neighbour into
+// that face's contiguous message, and an unpack kernel copies every message
+// block into the receiving box's ghost layers: the whole message for a face
+// neighbour, a sub-block of it (the first or last R rows or planes) for an
+// edge or corner neighbour, whose points the face messages hold too.  On one
+// GPU the unpack reads the sender's message directly; across GPUs a peer
+// copy (or NCCL send/recv) of each contiguous message into the receiver's
+// memory would come in between.  (Writing the messages from the step's own
+// epilogue was measured 1.7x slower than the plain step: the extra code made
+// the kernel's hot loop execute 1.25x the instructions even for points that
+// store nothing; the two copy kernels cost a fraction of that.)  Every point
+// goes through the same arithmetic as in the undecomposed run, so both give
+// the same wavefields and receivers bit for bit.
 #include <string.h>
 
 #include <algorithm>
@@ -38,6 +44,7 @@
 
 #include "fd_aux.h"
 #include "fd_runtime.h"
+#include "fd_sched.h"
 
 namespace fd {
 
@@ -54,16 +61,16 @@ struct Box {
   int nb[27];           // neighbour box per direction (dx+1) + 3(dy+1) + 9(dz+1), -1: none
 };
 
-// One unpack block of n0 x n1 x n2 points: from a face message (row stride
-// r1, plane stride r2 within it: the whole message or a sub-block of it) into
-// a strided region of the receiving box's wavefield (buffer chosen per step).
+// One block copy of n0 x n1 x n2 points between strided regions (row and
+// plane strides in floats); the side that is a box wavefield has one address
+// per buffer of the pair, the step's parity chooses.  Pack: box -> message;
+// unpack: message (or a sub-block of it) -> box ghost layers.
 struct Msg {
-  const float* src;
+  const float* src[2];
   float* dst[2];
   int n0, n1, n2;
-  int r1, r2;        // source strides (floats)
-  int s1;            // destination row pitch (floats)
-  long long s2;      // destination plane stride (floats)
+  long long s1, s2;  // source strides
+  long long d1, d2;  // destination strides
 };
 
 struct Cart {
@@ -72,8 +79,12 @@ struct Cart {
   std::vector<Box> box;
   TileShape shape = {};
   DevBuf desc;   // ShotDesc per box, then the unit prefix
-  DevBuf msgs;   // Msg list
-  int nmsg = 0, maxlen = 0;  // messages; most rows in one
+  DevBuf msgs;   // pack blocks, then unpack blocks
+  int npack = 0, nunpack = 0, maxlen = 0;  // block counts; most points in one block
+  DevBuf sched;  // column-wave work items over all boxes: CTA starts, then items
+  long long sched_key[3] = {0, 0, 0};  // tile x, tile y, slots of the schedule
+  int sched_ctas = 0;
+  size_t sched_off = 0;
   bool graph_valid = false;
   cudaGraphExec_t gexec = nullptr;
   std::vector<char> gkey;
@@ -82,17 +93,17 @@ struct Cart {
 
 namespace {
 
-// Messages are at most (600 + 2R)^2 * R points, so 32-bit indices suffice
-// within one; the outer loop runs over the message's rows.
-__global__ void k_unpack(const Msg* __restrict__ msgs, int nb) {
-  const Msg m = msgs[blockIdx.y];
+// Block copies, one block per blockIdx.y: every point of a block is one
+// thread's (32-bit indices: a block holds at most (N + 2R)^2 R points).
+__global__ void k_copy_blocks(const Msg* __restrict__ list, int nb) {
+  const Msg m = list[blockIdx.y];
+  const int n = m.n0 * m.n1 * m.n2;
+  const float* src = m.src[nb];
   float* dst = m.dst[nb];
-  const int rows = m.n1 * m.n2;
-  for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < rows; r += gridDim.x * blockDim.y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int i0 = i % m.n0, r = i / m.n0;
     const int i1 = r % m.n1, i2 = r / m.n1;
-    float* d = dst + i2 * m.s2 + static_cast<long long>(i1) * m.s1;
-    const float* sp = m.src + static_cast<long long>(i2) * m.r2 + static_cast<long long>(i1) * m.r1;
-    for (int i0 = threadIdx.x; i0 < m.n0; i0 += blockDim.x) d[i0] = sp[i0];
+    dst[i2 * m.d2 + i1 * m.d1 + i0] = src[i2 * m.s2 + i1 * m.s1 + i0];
   }
 }
 
@@ -120,6 +131,7 @@ void release(fd_grid g, Cart* c) {
   }
   c->desc.release();
   c->msgs.release();
+  c->sched.release();
   if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
   delete c;
 }
@@ -298,19 +310,48 @@ fd_status gather(fd_grid g, Cart* c) {
   return FD_OK;
 }
 
-// Unpack list: box b's ghost block towards direction d is the neighbour n
-// = b + d's owned block next to b: along an axis with d = 0 the owned range,
-// with d = -1 the R layers below b's first owned one (n's last R), with d = +1
-// the R above b's last (n's first R).  That block lies in one of n's face
-// messages, the one of the first axis a with d_a != 0 (n's face towards b on
-// that axis, f = 2a + (d_a < 0)): the whole message for a face neighbour, a
-// sub-block of it (the first or last R rows or planes of the other axes) for
-// an edge or corner neighbour.
+// Pack list: face f of box b (axis f / 2, low side for even f), where it has
+// a neighbour, copies b's R owned layers next to it into its message, stored
+// [z][y][x] over that block.  Unpack list: box b's ghost block towards
+// direction d is the neighbour n = b + d's owned block next to b: along an
+// axis with d = 0 the owned range, with d = -1 the R layers below b's first
+// owned one (n's last R), with d = +1 the R above b's last (n's first R).
+// That block lies in one of n's face messages, the one of the first axis a
+// with d_a != 0 (n's face towards b on that axis): the whole message for a
+// face neighbour, a sub-block of it (the first or last R rows or planes of
+// the other axes) for an edge or corner neighbour.
 fd_status build_messages(fd_grid g, Cart* c) {
   const int R = g->R;
   const int first[3] = {c->gx, R, R};
-  std::vector<Msg> list;
+  std::vector<Msg> pack, unpack;
   c->maxlen = 0;
+  for (Box& b : c->box) {
+    const long long row = b.pitch, plane = (long long)b.pitch * b.ay;
+    for (int f = 0; f < 6; ++f) {
+      if (!b.msg[f]) continue;
+      const int ax = f / 2;
+      int e[3], o[3];
+      for (int a = 0; a < 3; ++a) {
+        e[a] = a == ax ? R : b.on[a];
+        o[a] = first[a] + (a == ax && (f & 1) ? b.on[a] - R : 0);
+      }
+      Msg m;
+      const long long off = o[2] * plane + o[1] * row + o[0];
+      for (int q = 0; q < 2; ++q) {
+        m.src[q] = b.F.u[q] + off;
+        m.dst[q] = b.msg[f];
+      }
+      m.n0 = e[0];
+      m.n1 = e[1];
+      m.n2 = e[2];
+      m.s1 = row;
+      m.s2 = plane;
+      m.d1 = e[0];
+      m.d2 = (long long)e[0] * e[1];
+      pack.push_back(m);
+      c->maxlen = std::max(c->maxlen, e[0] * e[1] * e[2]);
+    }
+  }
   for (Box& b : c->box) {
     for (int k = 0; k < 27; ++k) {
       if (k == 13 || b.nb[k] < 0) continue;
@@ -319,8 +360,8 @@ fd_status build_messages(fd_grid g, Cart* c) {
       int ax = 0;
       while (d[ax] == 0) ++ax;
       const int f = 2 * ax + (d[ax] < 0 ? 1 : 0);  // n's face towards b
-      // extents of the face message of n along x, y, z, and the first point
-      // of the block within it
+      // extents of n's face message, the first point of the block within
+      // it, the block's extents and its first point in b's arrays
       int me[3], mo[3], e[3], o[3];
       for (int a = 0; a < 3; ++a) {
         me[a] = a == ax ? R : n.on[a];
@@ -329,24 +370,29 @@ fd_status build_messages(fd_grid g, Cart* c) {
         o[a] = d[a] == 0 ? first[a] : (d[a] > 0 ? first[a] + b.on[a] : first[a] - R);
       }
       Msg m;
-      m.src = n.msg[f] + ((long long)mo[2] * me[1] + mo[1]) * me[0] + mo[0];
-      m.r1 = me[0];
-      m.r2 = me[0] * me[1];
+      const float* src = n.msg[f] + ((long long)mo[2] * me[1] + mo[1]) * me[0] + mo[0];
+      m.s1 = me[0];
+      m.s2 = (long long)me[0] * me[1];
       m.n0 = e[0];
       m.n1 = e[1];
       m.n2 = e[2];
-      m.s1 = b.pitch;
-      m.s2 = (long long)b.pitch * b.ay;
-      const long long off = (long long)o[2] * m.s2 + (long long)o[1] * b.pitch + o[0];
-      for (int q = 0; q < 2; ++q) m.dst[q] = b.F.u[q] + off;
-      list.push_back(m);
-      c->maxlen = std::max(c->maxlen, e[1] * e[2]);
+      m.d1 = b.pitch;
+      m.d2 = (long long)b.pitch * b.ay;
+      const long long off = (long long)o[2] * m.d2 + (long long)o[1] * b.pitch + o[0];
+      for (int q = 0; q < 2; ++q) {
+        m.src[q] = src;
+        m.dst[q] = b.F.u[q] + off;
+      }
+      unpack.push_back(m);
+      c->maxlen = std::max(c->maxlen, e[0] * e[1] * e[2]);
     }
   }
-  c->nmsg = int(list.size());
-  cudaError_t e = c->msgs.ensure(std::max<size_t>(16, list.size() * sizeof(Msg)));
-  if (!e && !list.empty())
-    e = cudaMemcpyAsync(c->msgs.p, list.data(), list.size() * sizeof(Msg),
+  c->npack = int(pack.size());
+  c->nunpack = int(unpack.size());
+  pack.insert(pack.end(), unpack.begin(), unpack.end());
+  cudaError_t e = c->msgs.ensure(std::max<size_t>(16, pack.size() * sizeof(Msg)));
+  if (!e && !pack.empty())
+    e = cudaMemcpyAsync(c->msgs.p, pack.data(), pack.size() * sizeof(Msg),
                         cudaMemcpyHostToDevice, g->stream);
   if (!e) e = cudaStreamSynchronize(g->stream);
   if (e) return cuda_fail(e, "message list upload");
@@ -429,10 +475,6 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
     a.offx = off_x(c, b);
     a.offy = off_y(g, b);
     a.offz = off_z(g, b);
-    for (int f = 0; f < 6; ++f) a.pack[f] = b.msg[f];
-    a.onx = b.on[0];
-    a.ony = b.on[1];
-    a.onz = b.on[2];
     prefix[i + 1] = prefix[i] + (long long)a.tiles_x * a.tiles_y * b.on[2];
   }
   cudaError_t e = c->desc.ensure(host.size());
@@ -450,13 +492,49 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
     columns += (long long)((b.on[0] + bx - 1) / bx) * ((b.on[1] + by - 1) / by);
     onz_min = std::min(onz_min, b.on[2]);
   }
-  const int ctas = lockstep_ctas(R, g->shape, kModePack, columns, onz_min);
+  int ctas = lockstep_ctas(R, g->shape, kModeForward, columns, onz_min);
+  // column waves over all boxes (the boxes one after another, as the shots of
+  // a batch), unless the grid asks for equal shares or a CTA count: the
+  // columns of a wave advance together, so the y and x halo rows that
+  // neighbouring columns share are read from L2
+  const WorkItem* items = nullptr;
+  const int32_t* item_start = nullptr;
+  if (g->sched_mode != FD_SCHED_SHARES && g->shape.ctas == 0) {
+    const int slots = sweep_ctas(R, g->shape, kModeForward);
+    const long long key[3] = {g->shape.tx, g->shape.ty, slots};
+    if (memcmp(key, c->sched_key, sizeof(key)) != 0 || !c->sched.p) {
+      std::vector<SchedGrid> grids;
+      for (int i = 0; i < nbox; ++i) {
+        const Box& b = c->box[i];
+        grids.push_back({i, ((b.on[0] + bx - 1) / bx) * ((b.on[1] + by - 1) / by), b.on[2]});
+      }
+      std::vector<int32_t> start;
+      std::vector<WorkItem> witems;
+      const int used = wave_schedule(grids, slots, R, start, witems);
+      const size_t off = (start.size() * 4 + 15) / 16 * 16;
+      e = c->sched.ensure(off + witems.size() * sizeof(WorkItem));
+      if (!e) e = cudaMemcpyAsync(c->sched.p, start.data(), start.size() * 4,
+                                  cudaMemcpyHostToDevice, g->stream);
+      if (!e)
+        e = cudaMemcpyAsync(static_cast<char*>(c->sched.p) + off, witems.data(),
+                            witems.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, g->stream);
+      if (!e) e = cudaStreamSynchronize(g->stream);
+      if (e) return cuda_fail(e, "box schedule upload");
+      memcpy(c->sched_key, key, sizeof(key));
+      c->sched_ctas = used;
+      c->sched_off = off;
+    }
+    item_start = static_cast<const int32_t*>(c->sched.p);
+    items = reinterpret_cast<const WorkItem*>(static_cast<const char*>(c->sched.p) +
+                                              c->sched_off);
+    ctas = c->sched_ctas;
+  }
   const int cur0 = g->F.cur;
   const bool use_graph = nsteps >= 2 && !g->no_graph;
   std::vector<char> key;
   {
-    long long v[10] = {nsteps, cur0, n0, nsrc > 0, nrec > 0, g->shape.tx, g->shape.ty, ctas,
-                       g->spin_limit, (long long)c->msgs.p};
+    long long v[11] = {nsteps, cur0, n0, nsrc > 0, nrec > 0, g->shape.tx, g->shape.ty, ctas,
+                       g->spin_limit, (long long)c->msgs.p, (long long)items};
     key.assign(reinterpret_cast<char*>(v), reinterpret_cast<char*>(v) + sizeof(v));
     const char* dp = reinterpret_cast<const char*>(&c->desc.p);
     key.insert(key.end(), dp, dp + sizeof(void*));
@@ -467,8 +545,8 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
     }
   }
   const bool reuse = use_graph && c->graph_valid && c->gkey == key;
-  // unpack: 8 rows of a message per block of 32 x 8 threads
-  const int ublocks = std::max(1, std::min(2048, (c->maxlen + 7) / 8));
+  // copy kernels: 256 threads, enough blocks to cover the largest block copy
+  const int cblocks = std::max(1, std::min(1024, (c->maxlen + 255) / 256));
 
   auto issue = [&](cudaStream_t s) -> fd_status {
     const ShotDesc* sd = static_cast<const ShotDesc*>(c->desc.p);
@@ -484,12 +562,20 @@ fd_status cart_propagate(fd_grid g, int n0, int nsteps, const fd_points* src,
       ov.rec_row = t;
       ov.spin_limit = g->spin_limit;
       ov.debug_skip_plane = -1;
+      ov.item_start = item_start;
+      ov.items = items;
       launch_weights(g->c, R, ov.c);
-      cudaError_t e2 = launch_sweep(R, g->shape, kModePack, sd, pf, nbox, ov, ctas, s);
-      if (!e2 && c->nmsg > 0) {
+      cudaError_t e2 = launch_sweep(R, g->shape, kModeForward, sd, pf, nbox, ov, ctas, s);
+      // pack the faces of the buffer the step wrote, then unpack into it
+      const Msg* list = static_cast<const Msg*>(c->msgs.p);
+      if (!e2 && c->npack > 0) {
         count_launch();
-        k_unpack<<<dim3(ublocks, c->nmsg), dim3(32, 8), 0, s>>>(
-            static_cast<const Msg*>(c->msgs.p), ov.cur ^ 1);
+        k_copy_blocks<<<dim3(cblocks, c->npack), 256, 0, s>>>(list, ov.cur ^ 1);
+        e2 = cudaGetLastError();
+      }
+      if (!e2 && c->nunpack > 0) {
+        count_launch();
+        k_copy_blocks<<<dim3(cblocks, c->nunpack), 256, 0, s>>>(list + c->npack, ov.cur ^ 1);
         e2 = cudaGetLastError();
       }
       if (e2) return cuda_fail(e2, "decomposed step");

@@ -33,10 +33,8 @@ enum StepMode : int {
   kModeStoreE = 1,     // also e = (dt^2/m)(L u + s) for the imaging condition
   kModeAdjoint = 2,    // also grad -= u_cur * e_in / dt^2 (u_cur = z^{n+1})
   kModePerCell = 3,    // forward with per-cell weights c_1..c_R (space order 8)
-  kModeTable = 4,      // forward with weights c_1..c_4 interpolated per point from a
+  kModeTable = 4       // forward with weights c_1..c_4 interpolated per point from a
                        // table over A = (v dt / h)^2 (space order 8)
-  kModePack = 5        // forward, and the R updated layers next to each face of a
-                       // subdomain also written to that face's message buffer
 };
 
 // Everything one launch of the step kernel needs besides the tensor maps.
@@ -75,12 +73,6 @@ struct StepArgs {
   // array coordinate plus (offx, offy, offz), which places the damping layer.
   int32_t xfirst, yfirst, xend, yend;
   int32_t offx, offy, offz;
-  // kModePack: message buffers of the faces x-, x+, y-, y+, z-, z+ (nullptr:
-  // no neighbour there) and the owned extents; face f holds the R owned
-  // layers next to it, [z][y][j] for the x faces, [z][j][x] for y, [j][y][x]
-  // for z (j counted from the face's low side).
-  float* pack[6];
-  int32_t onx, ony, onz;
 };
 
 // One grid of a sweep launch (device memory): its tensor maps, constants and

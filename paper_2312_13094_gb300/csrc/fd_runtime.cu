@@ -585,7 +585,7 @@ int grid_schedule(fd_grid g, int mode, StepOverride* ov, fd_status* st) {
   *st = FD_OK;
   const bool tuned_waves = g->sched_mode == FD_SCHED_AUTO && g->tuned && g->tuned_waves &&
                            g->shape.tx == g->tuned_shape.tx && g->shape.ty == g->tuned_shape.ty;
-  if (mode != kModeForward || g->shape.ctas > 0 ||
+  if (mode == kModePerCell || g->shape.ctas > 0 ||
       !(g->sched_mode == FD_SCHED_WAVES || tuned_waves))
     return 0;
   const int slots = sweep_ctas(g->R, g->shape, mode);
@@ -629,7 +629,7 @@ fd_status use_shape(fd_grid g, bool plain_forward) {
   return build_maps(g);
 }
 
-// Tuner picks per (device, radius, padded size).
+// Tuner picks per (device, radius, padded size, kernel mode).
 static std::mutex g_tune_mu;
 static std::map<std::string, std::pair<TileShape, bool>> g_tune_cache;
 
@@ -638,7 +638,7 @@ fd_status autotune_grid(fd_grid g) {
   cudaGetDeviceProperties(&prop, g->d.device);
   const std::string key = std::string(prop.name) + "|R" + std::to_string(g->R) + "|" +
                           std::to_string(g->Nx) + "x" + std::to_string(g->Ny) + "x" +
-                          std::to_string(g->Nz);
+                          std::to_string(g->Nz) + "|M" + std::to_string(forward_mode(g));
   std::pair<TileShape, bool> pick = {g->base_shape, false};
   bool found = false;
   {
@@ -723,7 +723,8 @@ fd_status run_steps(fd_grid g, const RunSpec& rs) {
     const int Gs = grid_schedule(g, mode, &sched_ov, &st);
     if (st) return st;
     if (Gs > 0) G = Gs;
-    if (mode == kModeForward) g->last_sched = Gs > 0 ? FD_SCHED_WAVES : FD_SCHED_SHARES;
+    if (mode == kModeForward || mode == kModeTable)
+      g->last_sched = Gs > 0 ? FD_SCHED_WAVES : FD_SCHED_SHARES;
   }
   // descriptor + unit prefix, refreshed before every run (stream ordered),
   // so a captured graph stays valid when tables or caller arrays move
@@ -1064,7 +1065,9 @@ static fd_status propagate_impl(fd_grid g, int32_t n0, int32_t nsteps, const fd_
   const int nsrc = src ? src->n : 0, nrec = rec ? rec->n : 0;
   if ((nsrc && (!src->xyz || !wavelet)) || (nrec && (!rec->xyz || !rec_out)))
     return fail(FD_ERR_ARG, "points given without their data array");
-  fd_status st = use_shape(g, !g->dmp && !g->cart && forward_mode(g) == kModeForward);
+  // plain and table-weight forward runs take the tuner's pick (tile and
+  // schedule) for the grid's size; per-cell weight fields keep the base tile
+  fd_status st = use_shape(g, !g->dmp && !g->cart && forward_mode(g) != kModePerCell);
   if (st) return st;
   if (g->dmp) return decomp_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
   if (g->cart) return cart_propagate(g, n0, nsteps, src, wavelet, rec, rec_out);
@@ -1136,10 +1139,11 @@ fd_status fd_forward(fd_grid g, const fd_points* src, const float* wavelet,
     if (e) return cuda_fail(e, "wavefield reset");
   }
   g->F.cur = 0;
-  // plain forward runs of grids left on the default tile are tuned once, on
-  // the zeroed wavefields, which are cleared again afterwards
+  // plain and table-weight forward runs of grids left on the default tile
+  // are tuned once (on the grid's own kernel), on the zeroed wavefields,
+  // which are cleared again afterwards
   if (g->auto_tile && !g->tuned && g->sched_mode == FD_SCHED_AUTO && !g->dmp && !g->cart &&
-      forward_mode(g) == kModeForward && g->d.nt >= kTuneMinSteps && g->debug_skip_plane < 0) {
+      forward_mode(g) != kModePerCell && g->d.nt >= kTuneMinSteps && g->debug_skip_plane < 0) {
     fd_status st = autotune_grid(g);
     if (st) return st;
     for (int b = 0; b < 2; ++b) {
@@ -1221,6 +1225,7 @@ fd_status fd_set_coefficients(fd_grid g, const float* c, int32_t mode) {
   cudaSetDevice(g->d.device);
   g->graph_valid = false;
   g->table_mode = false;
+  g->tuned = false;  // the tuner's pick is per kernel mode: picked again
   if (mode == FD_COEF_TAYLOR) {
     fd_weights(g->R, g->c);
     g->percell = false;
@@ -1266,6 +1271,7 @@ fd_status fd_set_learned_coefficients(fd_grid g, fd_mlp net, double f_hz) {
   g->percell = true;
   g->table_mode = false;
   g->graph_valid = false;
+  g->tuned = false;
   return FD_OK;
 }
 
@@ -1313,6 +1319,7 @@ fd_status fd_set_learned_table(fd_grid g, fd_mlp net, double f_hz, int32_t nodes
   g->table_mode = true;
   g->percell = false;
   g->graph_valid = false;
+  g->tuned = false;
   return FD_OK;
 }
 

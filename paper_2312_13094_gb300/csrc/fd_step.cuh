@@ -279,32 +279,6 @@ __device__ __forceinline__ void update4_layer(const float lap[4], const float sr
   }
 }
 
-// kModePack epilogue: the updated values of four owned points (owned
-// coordinates ox..ox+3, oy, oz) within R layers of a face with a neighbour
-// also go to that face's message.  Faces only: the edge and corner ghosts of
-// a box are filled from sub-blocks of its diagonal neighbours' face messages,
-// which hold those points too.  zlo / zhi: oz is within R of the z faces.
-template <int R>
-__device__ __forceinline__ void pack_faces(const StepArgs& a, const float res[4], int ox, int oy,
-                                           int oz, bool zlo, bool zhi) {
-  const bool ylo = oy < R, yhi = oy >= a.ony - R;
-#pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const int x = ox + l;
-    if (x >= a.onx) break;
-    const float v = res[l];
-    if (x < R && a.pack[0]) a.pack[0][(static_cast<size_t>(oz) * a.ony + oy) * R + x] = v;
-    if (x >= a.onx - R && a.pack[1])
-      a.pack[1][(static_cast<size_t>(oz) * a.ony + oy) * R + (x - (a.onx - R))] = v;
-    if (ylo && a.pack[2]) a.pack[2][(static_cast<size_t>(oz) * R + oy) * a.onx + x] = v;
-    if (yhi && a.pack[3])
-      a.pack[3][(static_cast<size_t>(oz) * R + (oy - (a.ony - R))) * a.onx + x] = v;
-    if (zlo && a.pack[4]) a.pack[4][(static_cast<size_t>(oz) * a.ony + oy) * a.onx + x] = v;
-    if (zhi && a.pack[5])
-      a.pack[5][(static_cast<size_t>(oz - (a.onz - R)) * a.ony + oy) * a.onx + x] = v;
-  }
-}
-
 // One CTA: the xy tile (tile_x, tile_y), output planes [zbeg, zend).  All
 // threads of the CTA must call this with the same arguments.
 //
@@ -452,10 +426,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx;
     const bool in_grid = gy < a.yend && gx < a.xend;
-    // kModePack: the thread's points lie within R columns or rows of a face
-    const bool xy_edge = MODE == kModePack &&
-                         (gx - a.xfirst < R || gx - a.xfirst + 3 >= a.onx - R ||
-                          gy - a.yfirst < R || gy - a.yfirst >= a.ony - R);
     const float c0hi = ov.c[0], c0lo = ov.c[kMaxR + 1];  // centre weight (launch_weights)
     // the layer in array coordinates (shifted for subdomains)
     const int nblx = a.nbl - a.offx, nbly = a.nbl - a.offy, nblz = ov.nblz - a.offz;
@@ -496,7 +466,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     // up to SO 8 two planes per loop trip: the compiler renames the queue for
     // the first of them instead of shifting it (measured +2 % on 592^3 SO 8;
     // the wider stencils would spill)
-    constexpr int kUnroll = R <= 4 ? 2 : 1;
+    constexpr int kUnroll = (R <= 4 && MODE != kModePerCell) ? 2 : 1;
 #pragma unroll kUnroll
     for (int k = zbeg; k < zend; ++k) {
       {
@@ -552,6 +522,27 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                 ct[l][jj - 1] = fmaf(f, lane(dt, jj - 1), lane(t0, jj - 1));
             }
           }
+          if (MODE == kModeTable) {
+            // lane by lane (the sixteen interpolated weights stay live: as
+            // packed pairs they would spill)
+#pragma unroll
+            for (int jj = 1; jj <= R; ++jj) {
+              const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
+              const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+#pragma unroll
+              for (int l = 0; l < 4; ++l) {
+                const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
+                const float sy = lane(ym, l) + lane(yp, l);
+                const float sz = lane(zq(-jj), l) + lane(zq(jj), l);
+                const float d = fmaf(-6.0f, xr[C::RX + l], (sx + sy) + sz);
+                lap[l] = (jj == 1) ? ct[l][jj - 1] * d : fmaf(ct[l][jj - 1], d, lap[l]);
+              }
+            }
+          } else {
+          // per-cell weights: lanes (0,1) and (2,3) as packed pairs, each with
+          // its own weights (the roundings of the scalar form, lane by lane)
+          const float2 m6 = make_float2(-6.0f, -6.0f);
+          float2 lp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
           for (int jj = 1; jj <= R; ++jj) {
             float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -560,15 +551,26 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                                     ctile);
             const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
             const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+            const float4 zm = zq(-jj), zp = zq(jj);
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-              const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
-              const float sy = lane(ym, l) + lane(yp, l);
-              const float sz = lane(zq(-jj), l) + lane(zq(jj), l);
-              const float cj = (MODE == kModeTable) ? ct[l][jj - 1] : lane(cv, l);
-              const float d = fmaf(-6.0f, xr[C::RX + l], (sx + sy) + sz);
-              lap[l] = (jj == 1) ? cj * d : fmaf(cj, d, lap[l]);
+            for (int p = 0; p < 2; ++p) {
+              const int xa = C::RX + 2 * p - jj, xb = C::RX + 2 * p + jj;
+              const float2 sx =
+                  (jj & 1) ? make_float2(__fadd_rn(xr[xa], xr[xb]), __fadd_rn(xr[xa + 1], xr[xb + 1]))
+                           : __fadd2_rn(make_float2(xr[xa], xr[xa + 1]),
+                                        make_float2(xr[xb], xr[xb + 1]));
+              const float2 sy = __fadd2_rn(half2of(ym, p), half2of(yp, p));
+              const float2 sz = __fadd2_rn(half2of(zm, p), half2of(zp, p));
+              const float2 u2 = make_float2(xr[C::RX + 2 * p], xr[C::RX + 2 * p + 1]);
+              const float2 d = __ffma2_rn(m6, u2, __fadd2_rn(__fadd2_rn(sx, sy), sz));
+              const float2 cj = half2of(cv, p);
+              lp[p] = (jj == 1) ? __fmul2_rn(cj, d) : __ffma2_rn(cj, d, lp[p]);
             }
+          }
+          lap[0] = lp[0].x;
+          lap[1] = lp[0].y;
+          lap[2] = lp[1].x;
+          lap[3] = lp[1].y;
           }
         } else {
           lap4_packed<R, C::RX>(
@@ -624,12 +626,6 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             g.z -= uc.z * ein.z * a.inv_dt2;
             g.w -= uc.w * ein.w * a.inv_dt2;
             *reinterpret_cast<float4*>(a.grad + off) = g;
-          }
-          if (MODE == kModePack) {
-            const int oz = k - ov.zfirst;
-            const bool zlo = oz < R, zhi = oz >= a.onz - R;
-            if (xy_edge || zlo || zhi)
-              pack_faces<R>(a, res, gx - a.xfirst, gy - a.yfirst, oz, zlo, zhi);
           }
         }
         off += plane_stride;

@@ -34,17 +34,18 @@ cudaError_t set_smem_attr() {
   return e;
 }
 
-// The scheduled sweep (forward mode only): the same shared memory and launch
-// bounds as the equal-share kernel, so the same CTAs fit on an SM.
-template <int R, int TX, int TY, int PF>
+// The scheduled sweep (every mode but per-cell weights): the same shared
+// memory and launch bounds as the equal-share kernel, so the same CTAs fit on
+// an SM.
+template <int R, int TX, int TY, int PF, int MODE>
 cudaError_t set_sched_smem_attr() {
   static unsigned long long done = 0;  // one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
   if (done & (1ull << (dev & 63))) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(sched_kernel<R, TX, TY, PF, kModeForward>,
+  cudaError_t e = cudaFuncSetAttribute(sched_kernel<R, TX, TY, PF, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       sweep_smem<R, TX, TY, PF, kModeForward>());
+                                       sweep_smem<R, TX, TY, PF, MODE>());
   if (e == cudaSuccess) done |= 1ull << (dev & 63);
   return e;
 }
@@ -53,8 +54,8 @@ template <int R, int TX, int TY, int PF, int MODE>
 cudaError_t launch_one(const ShotDesc* shots, const long long* prefix, int nshots,
                        const StepOverride& ov, int grid, cudaStream_t s) {
   if (ov.items) {
-    if constexpr (MODE == kModeForward) {
-      cudaError_t e = set_sched_smem_attr<R, TX, TY, PF>();
+    if constexpr (MODE != kModePerCell) {
+      cudaError_t e = set_sched_smem_attr<R, TX, TY, PF, MODE>();
       if (e != cudaSuccess) return e;
       sched_kernel<R, TX, TY, PF, MODE><<<grid, TX * TY, sweep_smem<R, TX, TY, PF, MODE>(), s>>>(
           shots, ov);
@@ -124,8 +125,6 @@ cudaError_t launch_sweep_r<FD_R>(const TileShape& t, int mode, const ShotDesc* s
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 1>(shots, prefix, nshots, ov, grid, s); \
       case kModeAdjoint:                                                                  \
         return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(shots, prefix, nshots, ov, grid, s); \
-      case kModePack:                                                                     \
-        return launch_one<FD_R, TX, TY, FD_PF(TX, TY), 5>(shots, prefix, nshots, ov, grid, s); \
       FD_PERCELL_LAUNCH(TX, TY)                                                           \
       default: return cudaErrorInvalidValue;                                              \
     }                                                                                     \
@@ -143,7 +142,6 @@ int sweep_blocks_per_sm_r<FD_R>(const TileShape& t, int mode) {
       case kModeForward: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 0>(); \
       case kModeStoreE: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 1>();  \
       case kModeAdjoint: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 2>(); \
-      case kModePack: return occupancy_one<FD_R, TX, TY, FD_PF(TX, TY), 5>();    \
       FD_PERCELL_OCC(TX, TY)                                                    \
       default: return 0;                                                        \
     }                                                                           \

@@ -83,6 +83,49 @@ def test_checkpoint_count_does_not_change_the_result(fd):
         np.testing.assert_array_equal(g, ref)
 
 
+def test_adjoint_schedules_and_tiles_agree_bitwise(fd):
+    """The recompute and adjoint sweeps on column waves (as the tuner may
+    pick them) and on equal shares, on three tiles: the same bits."""
+    w = problem(8, n=(70, 40, 36), nt=45)
+    d_obs = observed(w)
+
+    def grad_with(sched, tile):
+        with fd.Grid.from_workload(w) as g:
+            if tile is not None:
+                g.set_tile(tile[0], tile[1], 0)
+            g.set_schedule(sched)
+            g.set_model(w["v"])
+            grad = np.zeros(g.phys_shape, np.float32)
+            st, loss = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], d_obs, 5, grad)
+            fd.check(st, "fd_adjoint_gradient")
+            return grad, loss
+
+    ref = grad_with(fd.FD_SCHED_SHARES, None)
+    for sched, tile in ((fd.FD_SCHED_WAVES, (64, 16)), (fd.FD_SCHED_WAVES, (32, 8)),
+                        (fd.FD_SCHED_WAVES, None)):
+        grad, loss = grad_with(sched, tile)
+        np.testing.assert_array_equal(grad, ref[0])
+        assert loss == ref[1]
+
+
+def test_tuned_adjoint_equals_equal_shares(fd):
+    """A long adjoint run on a grid left on the default tile tunes the grid
+    (tile and schedule) first; its gradient is the equal-share one."""
+    w = problem(8, n=(60, 40, 36), nt=420)
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal((w["nt"], len(w["rec"]))).astype(np.float32)
+
+    def grad_with(sched):
+        with fd.Grid.from_workload(w) as g:
+            g.set_schedule(sched)
+            g.set_model(w["v"])
+            grad = np.zeros(g.phys_shape, np.float32)
+            fd.check(g.backward(w["src"], w["wavelet"], w["rec"], r, 20, grad), "fd_backward")
+            return grad
+
+    np.testing.assert_array_equal(grad_with(fd.FD_SCHED_AUTO), grad_with(fd.FD_SCHED_SHARES))
+
+
 def test_backward_is_the_vector_jacobian_product(fd):
     w = problem(8, nt=40)
     rng = np.random.default_rng(9)

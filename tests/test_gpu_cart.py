@@ -1,7 +1,8 @@
 """GPU runs of the Cartesian domain decomposition (fd_set_topology: px x py x
-pz boxes with ghost layers; one message per face, edge and corner neighbour,
-the paper's diagonal mode of Sec. III, packed in the step's epilogue and
-unpacked into the neighbours' ghost layers) through the C ABI.
+pz boxes with ghost layers, stepped in one launch on column waves or equal
+shares; six face messages packed after every step, and every ghost block,
+faces, edges and corners, unpacked from them in one exchange, Sec. III)
+through the C ABI.
 
 Every point of a box run goes through the same arithmetic as in the
 undecomposed run, so the two must agree bit for bit (receivers, final and
@@ -60,10 +61,12 @@ def box_workload(so, n=(53, 41, 37), nbl=5, nt=50, seed=9):
                 wavelet=np.ascontiguousarray(wav, np.float32))
 
 
-def run(fd, w, topo=None, tile=None, no_graph=False):
+def run(fd, w, topo=None, tile=None, no_graph=False, sched=None):
     with fd.Grid.from_workload(w) as g:
         if tile is not None:
             g.set_tile(tile[0], tile[1], 0)
+        if sched is not None:
+            g.set_schedule(sched)
         if topo is not None:
             g.set_topology(*topo)
         if no_graph:
@@ -87,6 +90,19 @@ def test_boxes_match_the_whole_grid_bitwise(fd, so, topo):
     assert np.abs(ref[0]).max() > 0
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("topo", [(2, 2, 1), (2, 2, 2), (1, 3, 2)])
+def test_box_schedules_and_tiles_agree_bitwise(fd, topo):
+    """Column waves over all boxes (the default) and equal shares, on three
+    tiles: every point is computed the same way whatever CTA computes it."""
+    w = box_workload(8, n=(70, 45, 39), nt=24)
+    ref = run(fd, w)
+    for sched, tile in ((fd.FD_SCHED_SHARES, None), (fd.FD_SCHED_WAVES, (64, 16)),
+                        (fd.FD_SCHED_WAVES, (32, 8)), (fd.FD_SCHED_AUTO, (128, 8))):
+        got = run(fd, w, topo, tile=tile, sched=sched)
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_receivers_on_box_edges_and_corners(fd):

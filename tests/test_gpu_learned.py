@@ -168,6 +168,35 @@ def test_learned_table_on_a_grid_matches_oracle(fd, learned, nodes):
     net.close()
 
 
+def test_table_mode_schedules_tiles_and_tuner_agree_bitwise(fd, learned):
+    """Table-weight steps on column waves and equal shares, on three tiles,
+    and a long run that tunes the grid on its own (table) kernel: the same
+    receivers bit for bit."""
+    w = _percell_workload()
+    net = learned.Network(mlp.init_params(9, scale_out=1.0).astype(np.float32))
+
+    def rec_with(sched, tile, nt=None):
+        ww = w if nt is None else _percell_workload(nt)
+        with fd.Grid.from_workload(ww) as g:
+            if tile is not None:
+                g.set_tile(tile[0], tile[1], 0)
+            g.set_schedule(sched)
+            g.set_model(ww["v"])
+            fd.check(fd.fd_set_learned_table(g.handle, net.handle, ww["f0"], 64), "table")
+            rec = np.zeros((ww["nt"], len(ww["rec"])), np.float32)
+            fd.check(g.forward(ww["src"], ww["wavelet"], ww["rec"], rec), "fd_forward")
+            return rec
+
+    ref = rec_with(fd.FD_SCHED_SHARES, None)
+    assert np.abs(ref).max() > 0
+    for sched, tile in ((fd.FD_SCHED_WAVES, (64, 16)), (fd.FD_SCHED_WAVES, (32, 8)),
+                        (fd.FD_SCHED_WAVES, None)):
+        np.testing.assert_array_equal(rec_with(sched, tile), ref)
+    long_ref = rec_with(fd.FD_SCHED_SHARES, None, nt=420)
+    np.testing.assert_array_equal(rec_with(fd.FD_SCHED_AUTO, None, nt=420), long_ref)
+    net.close()
+
+
 def test_table_mode_is_refused_by_the_adjoint_and_reset_by_plain_weights(fd, learned):
     w = _percell_workload()
     net = learned.Network(mlp.init_params(9, scale_out=1.0).astype(np.float32))

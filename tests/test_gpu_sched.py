@@ -106,11 +106,12 @@ def test_unknown_schedule_is_rejected(fd):
         assert e.value.status == fd.FD_ERR_ARG
 
 
-def test_tuner_keeps_the_bits_and_the_adjoint_keeps_its_tile(fd):
+def test_tuner_keeps_the_bits_for_forward_and_adjoint_runs(fd):
     """A grid left on its default tile is tuned by its first long fd_forward:
     the pick is a compiled tile under one of the two schedules, the receivers
     and wavefield equal an untuned run on the default tile bit for bit, and a
-    later adjoint gradient equals that of a grid that was never tuned."""
+    later adjoint gradient (run on the tuned tile and schedule) equals that of
+    a grid that was never tuned."""
     import torch
     w = workload(8, (60, 50, 44), 6, 420)
     rec0 = np.zeros((w["nt"], len(w["rec"])), np.float32)
@@ -136,6 +137,7 @@ def test_tuner_keeps_the_bits_and_the_adjoint_keeps_its_tile(fd):
         assert info["schedule"] in (fd.FD_SCHED_SHARES, fd.FD_SCHED_WAVES)
         st, loss1 = g.adjoint_gradient(w["src"], w["wavelet"], w["rec"], 0.5 * rec0, 5, g1)
         fd.check(st, "fd_adjoint_gradient")
+        assert (g.info()["tile_x"], g.info()["tile_y"]) == (info["tile_x"], info["tile_y"])
         # the tuned pair serves the next forward run again
         rec2 = np.zeros_like(rec0)
         fd.check(g.forward(w["src"], w["wavelet"], w["rec"], rec2), "fd_forward")
