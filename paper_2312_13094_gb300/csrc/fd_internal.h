@@ -79,7 +79,7 @@ struct StepArgs {
 // buffers.  Step-dependent values come from StepOverride.
 struct ShotDesc {
   CUtensorMap halo[2];  // u^n with halo, per buffer
-  CUtensorMap tile[2];  // u^{n-1} tiles, per buffer
+  CUtensorMap tile[2];  // tiles without halo, per buffer (u^{n-1}; u^n for R >= 5)
   CUtensorMap A;        // model term tiles
   CUtensorMap C;        // per-cell weight tiles (fields stacked along z) or A
   StepArgs args;

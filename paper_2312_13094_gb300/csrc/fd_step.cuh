@@ -19,6 +19,16 @@
 //  * u^{n-1} and A tiles come through a second TMA ring of PF + 1 slots.
 //  * z neighbours live in a per-thread register queue of 2R+1 float4s; x and
 //    y neighbours are read from the staged plane with 128-bit loads.
+//  * The wide stencils (R >= 5) split the u^n staging: the ring of halo
+//    tiles holds only the centre plane and PF planes ahead (SU = PF + 1),
+//    and the queue is fed R planes ahead of the centre from a third ring of
+//    PF + 1 interior tiles.  Each plane is then copied twice from L2 (once as
+//    an interior tile, R planes later with its halo), but a CTA holds
+//    2 (PF + 1) tiles instead of R + 1 + PF halo tiles, so that the
+//    512 threads per SM that the registers allow are not cut by shared
+//    memory (a 32 x 16 tile at R = 8: 70 KB per CTA, three CTAs per SM,
+//    with the single ring).
+//  * Shared memory is read with explicit ld.shared at 32-bit addresses.
 //  * Source injection and receiver interpolation use per-tile entry lists
 //    sorted by z, so a tile without points pays one compare per plane.
 //  * Every mbarrier wait is bounded (clock64); on expiry the CTA records an
@@ -39,8 +49,10 @@ struct Cfg {
   static constexpr int NT = TX * TY;
   static constexpr int W = BX + 2 * RX;
   static constexpr int H = BY + 2 * R;
-  static constexpr int SU = R + 1 + PF;
+  static constexpr bool SPLIT = R >= 5;  // split u^n staging (see above)
+  static constexpr int SU = SPLIT ? PF + 1 : R + 1 + PF;  // halo-tile slots
   static constexpr int SA = PF + 1;
+  static constexpr int SI = SPLIT ? PF + 1 : 0;  // interior-tile slots of u^n
   static constexpr uint32_t UBYTES = W * H * 4;
   static constexpr uint32_t UPITCH = (UBYTES + 127) / 128 * 128;
   static constexpr uint32_t TBYTES = BX * BY * 4;
@@ -48,9 +60,10 @@ struct Cfg {
   static constexpr uint32_t OFF_P = SU * UPITCH;
   static constexpr uint32_t OFF_A = OFF_P + SA * TPITCH;
   static constexpr uint32_t OFF_C = OFF_A + SA * TPITCH;      // NC coefficient tiles
-  static constexpr uint32_t OFF_BAR = OFF_C + SA * NC * TPITCH;
-  // full and empty barrier per ring slot
-  static constexpr uint32_t SMEM = OFF_BAR + 2 * (SU + SA) * 8 + 128;
+  static constexpr uint32_t OFF_I = OFF_C + SA * NC * TPITCH;  // u^n interior tiles
+  static constexpr uint32_t OFF_BAR = OFF_I + SI * TPITCH;
+  // one barrier per ring slot (twice the room: kept as before)
+  static constexpr uint32_t SMEM = OFF_BAR + 2 * (SU + SA + SI) * 8 + 128;
   static constexpr int NROW4 = 2 * RX / 4 + 1;
   static_assert(W <= 256 && H <= 256, "TMA box too large");
 };
@@ -79,9 +92,11 @@ constexpr int auto_pf() {
   const int rx = ((R + 3) / 4) * 4;
   const uint32_t up = ((4 * TX + 2 * rx) * (TY + 2 * R) * 4 + 127) / 128 * 128;
   const uint32_t tp = (4 * TX * TY * 4 + 127) / 128 * 128;
+  const bool split = R >= 5;
   for (int pf = 6; pf > 1; --pf) {
-    const uint32_t smem = (R + 1 + pf) * up + (pf + 1) * (2 + NC) * tp +
-                          2 * (R + 1 + pf + pf + 1) * 8 + 128;
+    const int su = split ? pf + 1 : R + 1 + pf, si = split ? pf + 1 : 0;
+    const uint32_t smem =
+        su * up + (pf + 1) * (2 + NC) * tp + si * tp + 2 * (su + pf + 1 + si) * 8 + 128;
     if (smem <= budget) return pf;
   }
   return 1;
@@ -89,6 +104,23 @@ constexpr int auto_pf() {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Loads from shared memory at a 32-bit shared address.  Volatile, so that no
+// load of a ring slot is merged with an earlier load of the same slot or
+// moved across the mbarrier wait that makes the slot's new plane visible.
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+
+__device__ __forceinline__ float lds1(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -290,6 +322,14 @@ __device__ __forceinline__ void update4_layer(const float lap[4], const float sr
 // jk mod SU with plane jk + SU and slot i mod SA with tile i + SA.  The slots
 // are tracked as byte offsets that advance by one pitch per plane.
 //
+// Split staging (R >= 5).  The halo ring holds the centre planes h = 0 .. zl
+// (z = zbeg + h; plane zl only for receivers of the last plane) in slot
+// h mod SU; the interior ring holds planes j = 0 .. J-1 (numbered as above)
+// in slot j mod SI.  The prologue takes planes 0 .. 2R-1 into the queue in
+// batches of SI, refilling the batch's slots after a barrier; output plane k
+// then takes plane jn = i + 2R from the interior ring and its x and y
+// neighbours from halo plane i.
+//
 // Register queue: q[R + o] holds the thread's own float4 of plane jk + o,
 // o = -R .. R; it shifts by one entry per plane.  (Unrolling the z loop by
 // 2R+1 so that the queue rotates by register naming instead was measured
@@ -297,6 +337,7 @@ __device__ __forceinline__ void update4_layer(const float lap[4], const float sr
 // against 280 Gpts/s on 592^3; two planes per block ran 1.5 % slower.)
 template <int R, int TX, int TY, int PF, int MODE>
 __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
+                                           const CUtensorMap* tm_cur,
                                            const CUtensorMap* tm_prev,
                                            const CUtensorMap* tm_A,
                                            const CUtensorMap* tm_C,
@@ -306,14 +347,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
                                            unsigned char* smem) {
   constexpr int NC = (MODE == kModePerCell) ? R : 0;
   using C = Cfg<R, TX, TY, PF, NC>;
-  // z neighbours: the wide stencils (R >= 5) keep only planes k-R .. k in the
-  // register queue and read the planes above from the ring, which holds them
-  // anyway (halving the queue's registers and its shift); the others keep all
-  // 2R+1 planes in registers
-  constexpr bool HALFQ = R >= 5;
-  constexpr int NQ = HALFQ ? R + 1 : 2 * R + 1;
-  constexpr uint32_t URING = C::SU * C::UPITCH;
-  constexpr uint32_t ARING = C::SA * C::TPITCH;
+  constexpr bool SPLIT = C::SPLIT;
+  constexpr int NQ = 2 * R + 1;
   const int tid = threadIdx.x;
   const int tx = tid % TX;
   const int ty = tid / TX;
@@ -333,10 +368,13 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar_u0 = sbase + C::OFF_BAR;
   const uint32_t bar_a0 = bar_u0 + 8 * C::SU;
-  const unsigned char* ubuf = smem;
-  const unsigned char* pbuf = smem + C::OFF_P;
-  const unsigned char* abuf = smem + C::OFF_A;
-  const unsigned char* cbuf = smem + C::OFF_C;
+  const uint32_t bar_i0 = bar_a0 + 8 * C::SA;
+  // shared addresses of the rings
+  const uint32_t ubuf = sbase;
+  const uint32_t pbuf = sbase + C::OFF_P;
+  const uint32_t abuf = sbase + C::OFF_A;
+  const uint32_t cbuf = sbase + C::OFF_C;
+  const uint32_t ibuf = sbase + C::OFF_I;
 
   // kModeTable: the weight table of this grid, read from every point's
   // Courant number (made visible by the barrier below)
@@ -347,20 +385,34 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   if (tid == 0) {
     for (int s = 0; s < C::SU; ++s) mbar_init(bar_u0 + 8 * s, 1);
     for (int s = 0; s < C::SA; ++s) mbar_init(bar_a0 + 8 * s, 1);
+    for (int s = 0; s < C::SI; ++s) mbar_init(bar_i0 + 8 * s, 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  // producer (thread 0): next plane / tile to issue
-  int ju_next = 0, ia_next = 0;
+  // producer (thread 0): next plane / tile to issue.  Halo tiles: planes
+  // j of the single ring, or centre planes h (z = zbeg + h) when split.
+  int ju_next = 0, ia_next = 0, ji_next = 0;
+  const int UN = SPLIT ? zl + 1 : J;
+  const int z_u0 = SPLIT ? zbeg : zbeg - R;
   auto issue_u = [&](int j, uint32_t uoff) {
-    if (j >= J) return;
+    if (j >= UN) return;
     ju_next = j + 1;
-    const int z = zbeg - R + j;
+    const int z = z_u0 + j;
     if (ov.debug_skip_plane >= 0 && z == ov.debug_skip_plane) return;
     const uint32_t bar = bar_u0 + 8 * (uoff / C::UPITCH);
     mbar_expect_tx(bar, C::UBYTES);
     tma_load_3d(sbase + uoff, tm_halo, x0 - C::RX, y0 - R, z, bar);
+  };
+  // interior tiles of u^n (split staging): plane j, z = zbeg - R + j
+  auto issue_i = [&](int j, uint32_t ioff) {
+    if (j >= J) return;
+    ji_next = j + 1;
+    const int z = zbeg - R + j;
+    if (ov.debug_skip_plane >= 0 && z == ov.debug_skip_plane) return;
+    const uint32_t bar = bar_i0 + 8 * (ioff / C::TPITCH);
+    mbar_expect_tx(bar, C::TBYTES);
+    tma_load_3d(ibuf + ioff, tm_cur, x0, y0, z, bar);
   };
   auto issue_a = [&](int i, uint32_t aoff) {
     if (i >= zl) return;
@@ -382,6 +434,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   static_assert(C::NT > kAuxTid, "CTAs have at least two warps");
   if (tid == 0) {
     for (int j = 0; j < C::SU; ++j) issue_u(j, j * C::UPITCH);
+    for (int j = 0; j < C::SI; ++j) issue_i(j, j * C::TPITCH);
   }
   if (tid == kAuxTid) {
     for (int i = 0; i < C::SA; ++i) issue_a(i, i * C::TPITCH);
@@ -393,14 +446,28 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
   float4 q[NQ];
   bool bad = false;
 
+  if constexpr (SPLIT) {
 #pragma unroll
-  for (int j = 0; j < 2 * R; ++j) {
-    const int slot = j % C::SU;
-    bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, ov.spin_limit);
-    if (!HALFQ || j < R) q[j] = *reinterpret_cast<const float4*>(ubuf + slot * C::UPITCH + crow);
-    if (j < R) {
-      if (__syncthreads_or(bad)) goto fail;
-      if (tid == 0) issue_u(j + C::SU, slot * C::UPITCH);
+    for (int j = 0; j < 2 * R; ++j) {
+      const int slot = j % C::SI;
+      bad |= !mbar_wait(bar_i0 + 8 * slot, (j / C::SI) & 1, ov.spin_limit);
+      q[j] = lds4(ibuf + slot * C::TPITCH + ctile);
+      if (slot == C::SI - 1 || j == 2 * R - 1) {
+        if (__syncthreads_or(bad)) goto fail;
+        if (tid == 0)
+          for (int jj = j - slot; jj <= j; ++jj) issue_i(jj + C::SI, (jj % C::SI) * C::TPITCH);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j) {
+      const int slot = j % C::SU;
+      bad |= !mbar_wait(bar_u0 + 8 * slot, (j / C::SU) & 1, ov.spin_limit);
+      q[j] = lds4(ubuf + slot * C::UPITCH + crow);
+      if (j < R) {
+        if (__syncthreads_or(bad)) goto fail;
+        if (tid == 0) issue_u(j + C::SU, slot * C::UPITCH);
+      }
     }
   }
 
@@ -456,44 +523,44 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     size_t off = (static_cast<size_t>(zbeg) * a.Ny + gy) * a.pitch + gx;
     const size_t plane_stride = static_cast<size_t>(a.Ny) * a.pitch;
 
-    // ring slots: sk holds plane jk, sn plane jn (parity pn), sa tile ik
-    int sk = R % C::SU;
-    int sn = (2 * R) % C::SU;
-    uint32_t pn = ((2 * R) / C::SU) & 1;
+    // ring slots: sk holds plane jk (split: halo plane ik, parity pk), sn
+    // plane jn (parity pn; split: in the interior ring), sa tile ik
+    constexpr int SN = SPLIT ? C::SI : C::SU;
+    int sk = SPLIT ? 0 : R % C::SU;
+    uint32_t pk = 0;
+    int sn = (2 * R) % SN;
+    uint32_t pn = ((2 * R) / SN) & 1;
     int sa = 0;
     uint32_t pa = 0;
 
-    // up to SO 8 two planes per loop trip: the compiler renames the queue for
-    // the first of them instead of shifting it (measured +2 % on 592^3 SO 8;
-    // the wider stencils would spill)
-    constexpr int kUnroll = (R <= 4 && MODE != kModePerCell) ? 2 : 1;
+    // two planes per loop trip: the compiler renames the queue for the first
+    // of them instead of shifting it (592^3: +2 % at SO 8, +7 % at SO 16,
+    // where the 17-entry queue's shift is 64 moves per plane); per-cell
+    // weights would spill
+    constexpr int kUnroll = (MODE != kModePerCell) ? 2 : 1;
 #pragma unroll kUnroll
     for (int k = zbeg; k < zend; ++k) {
       {
 #define FD_Q(o) q[R + (o)]
         const int ik = k - zbeg;
         const int jk = ik + R;
-        bad |= !mbar_wait(bar_u0 + 8 * sn, pn, ov.spin_limit);
-        if (HALFQ)
-          FD_Q(0) = *reinterpret_cast<const float4*>(ubuf + sk * C::UPITCH + crow);
-        else
-          q[2 * R] = *reinterpret_cast<const float4*>(ubuf + sn * C::UPITCH + crow);
+        if constexpr (SPLIT) {
+          bad |= !mbar_wait(bar_u0 + 8 * sk, pk, ov.spin_limit);
+          bad |= !mbar_wait(bar_i0 + 8 * sn, pn, ov.spin_limit);
+          q[2 * R] = lds4(ibuf + sn * C::TPITCH + ctile);
+        } else {
+          bad |= !mbar_wait(bar_u0 + 8 * sn, pn, ov.spin_limit);
+          q[2 * R] = lds4(ubuf + sn * C::UPITCH + crow);
+        }
         bad |= !mbar_wait(bar_a0 + 8 * sa, pa, ov.spin_limit);
-        // the float4 of the plane at z offset o (-R .. R): register queue, or
-        // for o > 0 with the half queue the ring slot holding it
-        auto zq = [&](int o) -> float4 {
-          if (!HALFQ || o <= 0) return q[R + o];
-          const int sl = sk + o >= C::SU ? sk + o - C::SU : sk + o;
-          return *reinterpret_cast<const float4*>(ubuf + sl * C::UPITCH + crow);
-        };
+        // the float4 of the plane at z offset o (-R .. R)
+        auto zq = [&](int o) -> float4 { return q[R + o]; };
 
-        const unsigned char* P = ubuf + sk * C::UPITCH + crow;
+        const uint32_t P = ubuf + sk * C::UPITCH + crow;
         float xr[4 * C::NROW4];
 #pragma unroll
         for (int m = 0; m < C::NROW4; ++m) {
-          const float4 v = (m == C::NROW4 / 2)
-                               ? FD_Q(0)
-                               : *reinterpret_cast<const float4*>(P + 16 * (m - C::NROW4 / 2));
+          const float4 v = (m == C::NROW4 / 2) ? FD_Q(0) : lds4(P + 16 * (m - C::NROW4 / 2));
           xr[4 * m + 0] = v.x;
           xr[4 * m + 1] = v.y;
           xr[4 * m + 2] = v.z;
@@ -508,7 +575,7 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           // A = (v dt / h)^2
           float ct[4][R];
           if (MODE == kModeTable) {
-            const float4 At = *reinterpret_cast<const float4*>(abuf + sa * C::TPITCH + ctile);
+            const float4 At = lds4(abuf + sa * C::TPITCH + ctile);
             const float top = static_cast<float>(a.tab_nodes - 1);
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
@@ -527,8 +594,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
             // packed pairs they would spill)
 #pragma unroll
             for (int jj = 1; jj <= R; ++jj) {
-              const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
-              const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+              const float4 ym = lds4(P - 4 * jj * C::W);
+              const float4 yp = lds4(P + 4 * jj * C::W);
 #pragma unroll
               for (int l = 0; l < 4; ++l) {
                 const float sx = xr[C::RX + l - jj] + xr[C::RX + l + jj];
@@ -547,10 +614,9 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           for (int jj = 1; jj <= R; ++jj) {
             float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (MODE == kModePerCell)
-              cv = *reinterpret_cast<const float4*>(cbuf + (sa * NC + (jj - 1)) * C::TPITCH +
-                                                    ctile);
-            const float4 ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
-            const float4 yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+              cv = lds4(cbuf + (sa * NC + (jj - 1)) * C::TPITCH + ctile);
+            const float4 ym = lds4(P - 4 * jj * C::W);
+            const float4 yp = lds4(P + 4 * jj * C::W);
             const float4 zm = zq(-jj), zp = zq(jj);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
@@ -576,8 +642,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           lap4_packed<R, C::RX>(
               xr,
               [&](int jj, float4& ym, float4& yp) {
-                ym = *reinterpret_cast<const float4*>(P - 4 * jj * C::W);
-                yp = *reinterpret_cast<const float4*>(P + 4 * jj * C::W);
+                ym = lds4(P - 4 * jj * C::W);
+                yp = lds4(P + 4 * jj * C::W);
               },
               zq, ov.c, c0hi, c0lo, lap);
         }
@@ -599,8 +665,8 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
           iz = ip < iend ? a.inj[ip].z : INT_MAX;
         }
 
-        const float4 up = *reinterpret_cast<const float4*>(pbuf + sa * C::TPITCH + ctile);
-        const float4 Av = *reinterpret_cast<const float4*>(abuf + sa * C::TPITCH + ctile);
+        const float4 up = lds4(pbuf + sa * C::TPITCH + ctile);
+        const float4 Av = lds4(abuf + sa * C::TPITCH + ctile);
         float res[4], ev[4];
         // the same explicit roundings in every mode and on both branches, so
         // that a recomputed segment reproduces the stored states bit for bit
@@ -635,17 +701,20 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         if (k == rz) {
           int rq = rp;
           while (rq < rend && a.recs[rq].z == k) ++rq;
-          const float* P0 = reinterpret_cast<const float*>(ubuf + sk * C::UPITCH);
-          const float* P1 =
-              reinterpret_cast<const float*>(ubuf + (sk + 1 == C::SU ? 0 : sk + 1) * C::UPITCH);
+          const int s1 = sk + 1 == C::SU ? 0 : sk + 1;
+          // split staging: halo plane ik + 1 is in flight, not yet waited for
+          if (SPLIT) bad |= !mbar_wait(bar_u0 + 8 * s1, s1 == 0 ? pk ^ 1u : pk, ov.spin_limit);
+          const uint32_t P0 = ubuf + sk * C::UPITCH;
+          const uint32_t P1 = ubuf + s1 * C::UPITCH;
           for (int e = rp + tid; e < rq; e += C::NT) {
             const RecEntry r = a.recs[e];
-            const int o = (r.ly + R) * C::W + r.lx + C::RX;
+            const uint32_t o = 4u * ((r.ly + R) * C::W + r.lx + C::RX);
+            constexpr uint32_t W4 = 4u * C::W;
             const float gx0 = 1.0f - r.fx, gy0 = 1.0f - r.fy;
-            const float p0 = gy0 * (gx0 * P0[o] + r.fx * P0[o + 1]) +
-                             r.fy * (gx0 * P0[o + C::W] + r.fx * P0[o + C::W + 1]);
-            const float p1 = gy0 * (gx0 * P1[o] + r.fx * P1[o + 1]) +
-                             r.fy * (gx0 * P1[o + C::W] + r.fx * P1[o + C::W + 1]);
+            const float p0 = gy0 * (gx0 * lds1(P0 + o) + r.fx * lds1(P0 + o + 4)) +
+                             r.fy * (gx0 * lds1(P0 + o + W4) + r.fx * lds1(P0 + o + W4 + 4));
+            const float p1 = gy0 * (gx0 * lds1(P1 + o) + r.fx * lds1(P1 + o + 4)) +
+                             r.fy * (gx0 * lds1(P1 + o + W4) + r.fx * lds1(P1 + o + W4 + 4));
             a.rec_out[static_cast<size_t>(a.rec_row) * a.rec_ncol + r.col] =
                 (1.0f - r.fz) * p0 + r.fz * p1;
           }
@@ -654,10 +723,18 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         }
 
         if (__syncthreads_or(bad)) goto fail;
-        if (tid == 0) issue_u(jk + C::SU, sk * C::UPITCH);
+        if (tid == 0) {
+          if constexpr (SPLIT) {
+            issue_u(ik + C::SU, sk * C::UPITCH);
+            issue_i(jk + R + C::SI, sn * C::TPITCH);
+          } else {
+            issue_u(jk + C::SU, sk * C::UPITCH);
+          }
+        }
         if (tid == kAuxTid) issue_a(ik + C::SA, sa * C::TPITCH);
         sk = (sk + 1 == C::SU) ? 0 : sk + 1;
-        sn = (sn + 1 == C::SU) ? 0 : sn + 1;
+        pk ^= (sk == 0) ? 1u : 0u;
+        sn = (sn + 1 == SN) ? 0 : sn + 1;
         pn ^= (sn == 0) ? 1u : 0u;
         sa = (sa + 1 == C::SA) ? 0 : sa + 1;
         pa ^= (sa == 0) ? 1u : 0u;
@@ -667,11 +744,18 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
       }
     }
   }
-  // every issued copy has been waited for; release the barriers so the
-  // shared memory can host the next column
+  // every issued copy has been waited for (split staging: but for halo
+  // plane zl, which only receivers on the last plane wait for, so thread 0
+  // waits for it here); release the barriers so the shared memory can host
+  // the next column
   if (tid == 0) {
+    if (SPLIT && ju_next > zl && !(ov.debug_skip_plane >= 0 && zend == ov.debug_skip_plane)) {
+      if (!mbar_wait(bar_u0 + 8 * (zl % C::SU), (zl / C::SU) & 1, ov.spin_limit))
+        atomicOr(a.err, 1);
+    }
     for (int s = 0; s < C::SU; ++s) mbar_inval(bar_u0 + 8 * s);
     for (int s = 0; s < C::SA; ++s) mbar_inval(bar_a0 + 8 * s);
+    for (int s = 0; s < C::SI; ++s) mbar_inval(bar_i0 + 8 * s);
   }
   __syncthreads();
   return;
@@ -681,8 +765,14 @@ fail:
   if (tid == 0) {
     atomicOr(a.err, 1);
     for (int j = max(0, ju_next - C::SU); j < ju_next; ++j) {
-      if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
+      if (ov.debug_skip_plane >= 0 && z_u0 + j == ov.debug_skip_plane) continue;
       mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, ov.spin_limit);
+    }
+    if (SPLIT) {
+      for (int j = max(0, ji_next - C::SI); j < ji_next; ++j) {
+        if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
+        mbar_wait(bar_i0 + 8 * (j % C::SI), (j / C::SI) & 1, ov.spin_limit);
+      }
     }
   }
   if (tid == kAuxTid) {
@@ -729,7 +819,8 @@ __global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
       sa.e_in = ov.e_in;
     }
     __syncthreads();
-    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->C, sa, ov,
+    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur], &S->tile[cur ^ 1], &S->A,
+                                    &S->C, sa, ov,
                                     S->u[cur ^ 1], tile % sa.tiles_x, tile / sa.tiles_x,
                                     zb + ov.zfirst, ze + ov.zfirst, smem);
     __syncthreads();
@@ -761,7 +852,8 @@ __global__ void __launch_bounds__(TX* TY, threads_per_sm(R, MODE) / (TX * TY))
       sa.e_in = ov.e_in;
     }
     __syncthreads();
-    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur ^ 1], &S->A, &S->C, sa, ov,
+    run_column<R, TX, TY, PF, MODE>(&S->halo[cur], &S->tile[cur], &S->tile[cur ^ 1], &S->A,
+                                    &S->C, sa, ov,
                                     S->u[cur ^ 1], w.tile % sa.tiles_x, w.tile / sa.tiles_x,
                                     w.zb + ov.zfirst, w.ze + ov.zfirst, smem);
     __syncthreads();
