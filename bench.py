@@ -421,7 +421,6 @@ def run_adjoint(args):
     import torch
     from paper_2312_13094_gb300 import binding as fd
     from paper_2312_13094_gb300 import workloads as wl
-    import oracle  # noqa: F401  (oracle only for the observed data below)
     w = wl.adjoint_256(n=args.n if args.n != 512 else 256, nt=args.nt if args.nt != 1000 else 500)
     w0 = wl.adjoint_256(n=w["n"][0], nt=w["nt"], anomaly=False)
     stream = torch.cuda.Stream()

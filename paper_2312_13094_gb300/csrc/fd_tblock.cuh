@@ -407,8 +407,12 @@ template <int R>
 __global__ void __launch_bounds__(TbGeom<R>::NT, 1)
     tblock_kernel(const TbDesc* __restrict__ D, const __grid_constant__ TbLaunch L) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  // aligned to 128 bytes by an offset from the shared array itself, so that
+  // the compiler keeps the address space and issues shared-memory loads and
+  // stores (through a pointer rebuilt from an integer it issued generic ones)
+  unsigned char* smem =
+      smem_raw + ((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw)) & 127u)) &
+                  127u);
   __shared__ TbArgs a;
   if (threadIdx.x == 0) a = D->args;
   __syncthreads();
