@@ -276,12 +276,13 @@ fd_status fd_set_tile(fd_grid grid, int32_t tile_x, int32_t tile_y, int32_t ctas
  *                    of the busiest CTA (a host-side simulation);
  *   FD_SCHED_AUTO    the default: equal shares, except that a grid left on
  *                    its default tile (no fd_set_tile call) is tuned by its
- *                    first fd_forward of at least 400 steps: every compiled
- *                    tile is timed under both schedules for a few
- *                    source-free steps on the zeroed wavefields (cleared
- *                    again before the run), and the fastest pair serves all
- *                    later plain forward runs of grids of that padded size
- *                    on that device (fd_forward and fd_propagate; the pick is
+ *                    first fd_forward, fd_adjoint_gradient or fd_backward of
+ *                    at least 400 steps: every compiled tile is timed under
+ *                    both schedules for a few source-free steps on the
+ *                    zeroed wavefields (cleared again before the run), twice,
+ *                    and the fastest pair serves all later runs of grids of
+ *                    that padded size and kernel mode on that device
+ *                    (fd_forward, fd_propagate and the adjoint; the pick is
  *                    cached per process; fd_grid_info shows the tile and
  *                    schedule in use).
  *   FD_SCHED_TEMPORAL  temporal blocking (the paper's Discussion, Sec. IV,
@@ -443,7 +444,10 @@ fd_status fd_tti_destroy(fd_tti grid);
  * order; strongly tilted media may need a larger margin). */
 fd_status fd_tti_set_model(fd_tti grid, const float* vp, const float* epsilon,
                            const float* delta, const float* theta, const float* phi);
-/* desc.nt steps from rest; wavelet [nt][src->n], rec_out [nt][rec->n] = I(p^n). */
+/* desc.nt steps from rest; wavelet [nt][src->n], rec_out [nt][rec->n] = I(p^n).
+ * Errors (here and in fd_tti_propagate): those of fd_forward; FD_ERR_TIMEOUT
+ * when a bounded wait of the step kernel for its staged planes ran out (the
+ * state is then undefined). */
 fd_status fd_tti_forward(fd_tti grid, const fd_points* src, const float* wavelet,
                          const fd_points* rec, float* rec_out);
 /* Continues from the current state for nsteps steps (wavelet rows

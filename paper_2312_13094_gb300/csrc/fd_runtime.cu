@@ -662,9 +662,16 @@ fd_status autotune_grid(fd_grid g) {
     rs.f = &g->F;
     rs.allow_graph = 0;
     rs.mode = kModeForward;
+    // every (tile, schedule) pair is timed twice, in one order and then in
+    // the reverse one, and keeps its faster time: one pass of short trials
+    // misranked pairs within a few percent of each other
     const int trial = 6;
+    constexpr int kPairs = 2 * kNumShapes;
+    float best_of[kPairs];
+    for (int c = 0; c < kPairs; ++c) best_of[c] = 1e30f;
     float best = 1e30f;
-    for (int c = 0; c < 2 * kNumShapes && !st; ++c) {
+    for (int r = 0; r < 2 * kPairs && !st; ++r) {
+      const int c = r < kPairs ? r : 2 * kPairs - 1 - r;
       const TileShape t = kShapes[c / 2];
       g->tuned = true;
       g->tuned_shape = t;
@@ -682,8 +689,9 @@ fd_status autotune_grid(fd_grid g) {
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, a, b);
-      if (ms < best) {
-        best = ms;
+      best_of[c] = std::min(best_of[c], ms);
+      if (r >= kPairs && best_of[c] < best) {
+        best = best_of[c];
         pick = {t, g->tuned_waves};
       }
     }

@@ -533,11 +533,12 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     int sa = 0;
     uint32_t pa = 0;
 
-    // two planes per loop trip: the compiler renames the queue for the first
-    // of them instead of shifting it (592^3: +2 % at SO 8, +7 % at SO 16,
-    // where the 17-entry queue's shift is 64 moves per plane); per-cell
-    // weights would spill
-    constexpr int kUnroll = (MODE != kModePerCell) ? 2 : 1;
+    // several planes per loop trip: the compiler renames the queue for all
+    // but the last of them instead of shifting it.  Measured on 592^3
+    // (Gpts/s, trips of 1 / 2 / 3 / 4 planes): SO 8 -, 350, 360, 345;
+    // SO 16 196, 210, 217, 220 (6: 204, 8: 212); SO 12 248, 261, 266, 277.
+    // Per-cell weights keep one plane per trip (more would spill).
+    constexpr int kUnroll = MODE == kModePerCell ? 1 : (R >= 5 ? 4 : 3);
 #pragma unroll kUnroll
     for (int k = zbeg; k < zend; ++k) {
       {

@@ -15,21 +15,20 @@
 // zero ghost, source scaling and trilinear points as in the isotropic path;
 // the source enters both fields, receivers interpolate p.
 //
-// Kernels (2.5D, one point per thread): a CTA owns a 32 x 8 xy tile and a run
-// of z planes; the planes k-R .. k+R of p and q with an R-wide xy halo sit in
-// a shared-memory ring of 2R+1 slots per field, refilled one plane per step
-// with coalesced loads (zero outside the grid: the read-only halo), so every
-// derivative, cross terms included, reads shared memory.  Up to space order 8
-// (k_tti_cire) the first x and y differences of each plane are computed once
-// when it enters and kept in rings of their own, so each cross derivative
-// costs 2R shared loads, and each new plane (and the update's per-point
-// model values) is read into registers one plane ahead, so that its global
-// loads overlap the compute of the plane before;
-// the wider stencils (k_tti_step), whose extra rings would not fit, form the
-// cross derivatives as first differences of first differences directly from
-// the u ring, 4R^2 loads each.  The model enters through six per-cell fields
-// (dt^2 v^2 / h^2, 1 + 2 eps, sqrt(1 + 2 delta) and the axis n), computed
-// once per model in double precision.
+// Kernels (2.5D, one point per thread, a CTA owning a 32 x 8 xy tile and a
+// run of z planes).  Up to space order 8, k_tti_q (fd_tti_q.cuh): each plane
+// of p and q enters once, by TMA, with an R-wide halo; its in-plane second
+// derivatives and its first x and y differences are formed then, and every z
+// sum (D_zz, D_xz, D_yz) runs over per-thread register queues, so shared
+// memory holds only the entering plane, one plane of first x differences and
+// the update's per-point tiles.  The wider stencils (k_tti_step below), whose
+// queues would not fit in registers, keep the planes k-R .. k+R in a
+// shared-memory ring of 2R+1 slots per field, refilled with coalesced loads
+// (zero outside the grid: the read-only halo), and form the cross
+// derivatives as first differences of first differences from that ring, 4R^2
+// loads each.  The model enters through six per-cell fields (dt^2 v^2 / h^2,
+// 1 + 2 eps, sqrt(1 + 2 delta) and the axis n), computed once per model in
+// double precision.
 #include <math.h>
 #include <string.h>
 
@@ -40,6 +39,7 @@
 #include "fd_aux.h"
 #include "fd_internal.h"
 #include "fd_runtime.h"
+#include "fd_tti_q.cuh"
 
 namespace fd {
 void fd_weights(int R, double* c);
@@ -64,6 +64,11 @@ struct fd_tti_s {
   float bscale = 0.0f;
   double c[kMaxR + 1] = {}, d1[kMaxR + 1] = {};
   DevBuf inj, rec, stage_val, stage_rec, stage_in, scratch;
+  DevBuf err;  // error word of the TMA kernel's bounded waits
+  // tensor maps of the TMA kernel (space orders up to 8), per buffer
+  CUtensorMap halo_p[2], halo_q[2], tile_p[2], tile_q[2], coef_map;
+  bool maps = false;
+  long long spin_limit = 0;
   int n_inj = 0, n_rec = 0;
   bool profiling = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -312,199 +317,6 @@ __global__ void k_tti_inject(const TtiInj* __restrict__ inj, int n, const float*
   atomicAdd(q + e.off, s);
 }
 
-// The same update for space orders up to 8 with the cross-plane sums shared
-// between points (the cross-iteration redundancy elimination the paper's
-// Devito passes perform, Sec. II): when a plane enters the ring, its first x
-// difference dx = sum_i d_i (u(x+i) - u(x-i)) is computed once on the tile
-// and its R halo rows, and its first y difference dy on the tile; then
-//     D_xy = sum_j d_j (dx(y+j) - dx(y-j))   on plane k,
-//     D_xz = sum_j d_j (dx_(k+j) - dx_(k-j)),  D_yz likewise from dy,
-// 2R shared loads each instead of 4R^2.  Rings per field: u (2R+1 planes with
-// the xy halo), dx (2R+1 planes, tile plus y halo), dy (2R+1 planes, tile).
-template <int R>
-struct Cire {
-  static constexpr int S = 2 * R + 1;
-  static constexpr int WU = kBX + 2 * R, HU = kBY + 2 * R, PU = WU * HU;
-  static constexpr int PX = kBX * HU;  // dx plane: tile columns, rows with halo
-  static constexpr int PY = kBX * kBY; // dy plane: the tile
-  static constexpr int FIELD = S * (PU + PX + PY);
-};
-
-template <int R>
-__global__ void __launch_bounds__(kBX* kBY) k_tti_cire(const __grid_constant__ TtiArgs a) {
-  using C = Cire<R>;
-  constexpr int S = C::S, WU = C::WU, PU = C::PU, PX = C::PX, PY = C::PY;
-  extern __shared__ float sm[];
-  float* ru[2] = {sm, sm + C::FIELD};                    // u rings of p and q
-  float* rx[2] = {ru[0] + S * PU, ru[1] + S * PU};        // dx rings
-  float* ry[2] = {rx[0] + S * PX, rx[1] + S * PX};        // dy rings
-  const float* src[2] = {a.p, a.q};
-  const int tid = threadIdx.x, tx = tid % kBX, ty = tid / kBX;
-  const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
-  const int z0 = blockIdx.z * a.zchunk;
-  const int z1 = min(z0 + a.zchunk, a.Nz);
-  const size_t plane = static_cast<size_t>(a.Ny) * a.pitch;
-  auto slot = [&](int z) {
-    const int s = z % S;
-    return s < 0 ? s + S : s;
-  };
-  // the thread's share of a plane of u, read from global memory into
-  // registers one iteration before it is stored (zero outside the grid)
-  constexpr int NT = kBX * kBY, NL = (PU + NT - 1) / NT;
-  float pre[2][NL];
-  auto fetch = [&](int z) {
-    const bool zin = z >= 0 && z < a.Nz;
-#pragma unroll
-    for (int t = 0; t < NL; ++t) {
-      const int i = tid + t * NT;
-      const int lx = i % WU, ly = i / WU, gx = x0 - R + lx, gy = y0 - R + ly;
-      const bool in = i < PU && zin && gx >= 0 && gx < a.Nx && gy >= 0 && gy < a.Ny;
-      const size_t o =
-          in ? static_cast<size_t>(z) * plane + static_cast<size_t>(gy) * a.pitch + gx : 0;
-#pragma unroll
-      for (int f = 0; f < 2; ++f) pre[f][t] = in ? src[f][o] : 0.f;
-    }
-  };
-  // the fetched plane z into its slot, then its first differences; two
-  // barriers
-  auto enter = [&](int z) {
-    const int sl = slot(z);
-#pragma unroll
-    for (int t = 0; t < NL; ++t) {
-      const int i = tid + t * NT;
-      if (i < PU) {
-#pragma unroll
-        for (int f = 0; f < 2; ++f) ru[f][sl * PU + i] = pre[f][t];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const float* du = ru[f] + sl * PU;
-      float* dx = rx[f] + sl * PX;
-      for (int i = tid; i < PX; i += kBX * kBY) {
-        const int lx = i % kBX, ly = i / kBX;
-        const float* row = du + ly * WU + lx + R;
-        float acc = 0.f;
-#pragma unroll
-        for (int q = 1; q <= R; ++q) acc = fmaf(a.d[q], row[q] - row[-q], acc);
-        dx[i] = acc;
-      }
-      const float* col = du + (ty + R) * WU + tx + R;
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 1; q <= R; ++q) acc = fmaf(a.d[q], col[q * WU] - col[-q * WU], acc);
-      ry[f][sl * PY + tid] = acc;
-    }
-    __syncthreads();
-  };
-  for (int z = z0 - R; z < z0 + R; ++z) {
-    fetch(z);
-    enter(z);
-  }
-  fetch(z0 + R);
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool inside = gx < a.Nx && gy < a.Ny;
-  const int cu = (ty + R) * WU + tx + R;  // own point in a u plane
-  const int cx = (ty + R) * kBX + tx;     // in a dx plane
-  const int dxy = depth(gx, a.nbl, a.nx) * depth(gx, a.nbl, a.nx) +
-                  depth(gy, a.nbl, a.ny) * depth(gy, a.nbl, a.ny);
-  // the update's eight values at the thread's point (six model fields and
-  // the previous p and q), read one plane ahead as well; a plane's previous
-  // p and q are only written by the thread that reads them, after the read
-  float pv[8] = {}, pv_next[8] = {};
-  auto fetch_point = [&](int z, float* out) {
-    if (!inside) return;
-    const size_t o = static_cast<size_t>(z) * plane + static_cast<size_t>(gy) * a.pitch + gx;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) out[f] = a.coef[f * a.ncell + o];
-    out[6] = a.pn[o];
-    out[7] = a.qn[o];
-  };
-  fetch_point(z0, pv);
-  for (int k = z0; k < z1; ++k) {
-    enter(k + R);
-    if (k + 1 < z1) {  // in flight during this plane's compute
-      fetch(k + R + 1);
-      fetch_point(k + 1, pv_next);
-    }
-    if (inside) {
-      const int s0 = slot(k);
-      float D[2][6];
-#pragma unroll
-      for (int f = 0; f < 2; ++f) {
-        const float* U0 = ru[f] + s0 * PU;
-        const float* X0 = rx[f] + s0 * PX;
-        const float u0 = U0[cu];
-        float xx = a.c[0] * u0, yy = a.c[0] * u0, zz = a.c[0] * u0;
-        float xy = 0.f, xz = 0.f, yz = 0.f;
-#pragma unroll
-        for (int j = 1; j <= R; ++j) {
-          int sp = s0 + j, sm_ = s0 - j;
-          sp = sp >= S ? sp - S : sp;
-          sm_ = sm_ < 0 ? sm_ + S : sm_;
-          xx = fmaf(a.c[j], U0[cu + j] + U0[cu - j], xx);
-          yy = fmaf(a.c[j], U0[cu + j * WU] + U0[cu - j * WU], yy);
-          zz = fmaf(a.c[j], ru[f][sp * PU + cu] + ru[f][sm_ * PU + cu], zz);
-          xy = fmaf(a.d[j], X0[cx + j * kBX] - X0[cx - j * kBX], xy);
-          xz = fmaf(a.d[j], rx[f][sp * PX + cx] - rx[f][sm_ * PX + cx], xz);
-          yz = fmaf(a.d[j], ry[f][sp * PY + tid] - ry[f][sm_ * PY + tid], yz);
-        }
-        D[f][0] = xx;
-        D[f][1] = yy;
-        D[f][2] = zz;
-        D[f][3] = xy;
-        D[f][4] = xz;
-        D[f][5] = yz;
-      }
-      const size_t o = static_cast<size_t>(k) * plane + static_cast<size_t>(gy) * a.pitch + gx;
-      const float A = pv[0], e2 = pv[1], dl = pv[2], nx = pv[3], ny = pv[4], nz = pv[5];
-      const float wxx = nx * nx, wyy = ny * ny, wzz = nz * nz;
-      const float wxy = 2.f * nx * ny, wxz = 2.f * nx * nz, wyz = 2.f * ny * nz;
-      const float* dp = D[0];
-      const float* dq = D[1];
-      const float lap_p = dp[0] + dp[1] + dp[2];
-      const float hz_p = wxx * dp[0] + wyy * dp[1] + wzz * dp[2] + wxy * dp[3] + wxz * dp[4] +
-                         wyz * dp[5];
-      const float hz_q = wxx * dq[0] + wyy * dq[1] + wzz * dq[2] + wxy * dq[3] + wxz * dq[4] +
-                         wyz * dq[5];
-      const float h0_p = lap_p - hz_p;
-      const float rp = e2 * h0_p + dl * hz_q;
-      const float rq = dl * h0_p + hz_q;
-      const int dz = depth(k, a.nbl, a.nz);
-      const float b = a.bscale * static_cast<float>(dxy + dz * dz);
-      const float pc = ru[0][s0 * PU + cu], qc = ru[1][s0 * PU + cu];
-      const float pm = pv[6], qm = pv[7];
-      a.pn[o] = (2.f * pc - (1.f - b) * pm + A * rp) / (1.f + b);
-      a.qn[o] = (2.f * qc - (1.f - b) * qm + A * rq) / (1.f + b);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int f = 0; f < 8; ++f) pv[f] = pv_next[f];
-  }
-}
-
-template <int R>
-constexpr size_t cire_smem() {
-  return 2u * Cire<R>::FIELD * sizeof(float);
-}
-
-template <int R>
-cudaError_t launch_cire(const TtiArgs& a, dim3 grid, cudaStream_t s) {
-  static unsigned long long done = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (!(done & (1ull << (dev & 63)))) {
-    cudaError_t e = cudaFuncSetAttribute(k_tti_cire<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(cire_smem<R>()));
-    if (e) return e;
-    done |= 1ull << (dev & 63);
-  }
-  k_tti_cire<R><<<grid, kBX * kBY, cire_smem<R>(), s>>>(a);
-  return cudaGetLastError();
-}
-
 template <int R>
 constexpr size_t tti_smem() {
   return 2u * (2 * R + 1) * (kBX + 2 * R) * (kBY + 2 * R) * sizeof(float);
@@ -526,13 +338,37 @@ cudaError_t launch_r(const TtiArgs& a, dim3 grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(int R, const TtiArgs& a, dim3 grid, cudaStream_t s) {
+template <int R>
+cudaError_t launch_q(const tti::QMaps& M, const tti::QArgs& qa, dim3 grid, cudaStream_t s) {
+  static unsigned long long done = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!(done & (1ull << (dev & 63)))) {
+    cudaError_t e = cudaFuncSetAttribute(tti::k_tti_q<R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(tti::QGeom<R>::SMEM));
+    if (e) return e;
+    done |= 1ull << (dev & 63);
+  }
+  tti::k_tti_q<R><<<grid, tti::kQT, tti::QGeom<R>::SMEM, s>>>(M, qa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_r(int R, const tti::QMaps& M, const tti::QArgs& qa, dim3 grid,
+                       cudaStream_t s) {
   count_launch();
   switch (R) {
-    case 1: return launch_cire<1>(a, grid, s);
-    case 2: return launch_cire<2>(a, grid, s);
-    case 3: return launch_cire<3>(a, grid, s);
-    case 4: return launch_cire<4>(a, grid, s);
+    case 1: return launch_q<1>(M, qa, grid, s);
+    case 2: return launch_q<2>(M, qa, grid, s);
+    case 3: return launch_q<3>(M, qa, grid, s);
+    case 4: return launch_q<4>(M, qa, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(int R, const TtiArgs& a, dim3 grid, cudaStream_t s) {
+  count_launch();
+  switch (R) {  // space orders up to 8 run k_tti_q (launch_q_r)
     case 5: return launch_r<5>(a, grid, s);
     case 6: return launch_r<6>(a, grid, s);
     case 7: return launch_r<7>(a, grid, s);
@@ -699,6 +535,40 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
   }
   const dim3 grid((t->Nx + kBX - 1) / kBX, (t->Ny + kBY - 1) / kBY,
                   (t->Nz + a.zchunk - 1) / a.zchunk);
+  // space orders up to 8: the TMA kernel with register queues; its z chunks
+  // are cut so that the launch fills at least four waves of two CTAs per SM
+  const bool qk = t->maps;
+  tti::QArgs qa;
+  memset(&qa, 0, sizeof(qa));
+  dim3 qgrid(1, 1, 1);
+  if (qk) {
+    qa.err = static_cast<int*>(t->err.p);
+    qa.Nx = t->Nx;
+    qa.Ny = t->Ny;
+    qa.Nz = t->Nz;
+    qa.pitch = t->pitch;
+    qa.nbl = t->d.nbl;
+    qa.nx = t->d.nx;
+    qa.ny = t->d.ny;
+    qa.nz = t->d.nz;
+    qa.spin_limit = t->spin_limit;
+    qa.bscale = t->bscale;
+    for (int j = 0; j <= kMaxR; ++j) {
+      qa.c[j] = a.c[j];
+      qa.d[j] = a.d[j];
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long cols = (long long)((t->Nx + tti::kQX - 1) / tti::kQX) *
+                           ((t->Ny + tti::kQY - 1) / tti::kQY);
+    const long long want = 4LL * 2 * std::max(sms, 1);
+    int chunks = int(std::max<long long>(1, (want + cols - 1) / cols));
+    chunks = std::min(chunks, std::max(1, t->Nz / (8 * t->R)));
+    qa.zchunk = (t->Nz + chunks - 1) / chunks;
+    qgrid = dim3((t->Nx + tti::kQX - 1) / tti::kQX, (t->Ny + tti::kQY - 1) / tti::kQY,
+                 (t->Nz + qa.zchunk - 1) / qa.zchunk);
+  }
   if (t->profiling) cudaEventRecord(t->ev0, t->stream);
   for (int s = 0; s < nsteps; ++s) {
     const int cur = t->cur;
@@ -711,7 +581,20 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
     a.q = t->q[cur];
     a.pn = t->p[cur ^ 1];
     a.qn = t->q[cur ^ 1];
-    if ((e = launch_step(t->R, a, grid, t->stream))) return cuda_fail(e, "TTI step launch");
+    if (qk) {
+      tti::QMaps M;
+      M.halo_p = t->halo_p[cur];
+      M.halo_q = t->halo_q[cur];
+      M.prev_p = t->tile_p[cur ^ 1];
+      M.prev_q = t->tile_q[cur ^ 1];
+      M.coef = t->coef_map;
+      qa.pn = a.pn;
+      qa.qn = a.qn;
+      e = launch_q_r(t->R, M, qa, qgrid, t->stream);
+    } else {
+      e = launch_step(t->R, a, grid, t->stream);
+    }
+    if (e) return cuda_fail(e, "TTI step launch");
     if (t->n_inj) {
       k_tti_inject<<<(t->n_inj + 127) / 128, 128, 0, t->stream>>>(
           static_cast<const TtiInj*>(t->inj.p), t->n_inj, dval + size_t(n0 + s) * nsrc, t->coef,
@@ -743,6 +626,16 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
   }
   e = cudaStreamSynchronize(t->stream);
   if (e) return cuda_fail(e, "stream synchronize");
+  if (qk && nsteps > 0) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, t->err.p, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "error word");
+    if (flag) {
+      cudaMemsetAsync(t->err.p, 0, sizeof(int), t->stream);
+      cudaStreamSynchronize(t->stream);
+      return fail(FD_ERR_TIMEOUT, "a bounded wait of the TTI step ran out");
+    }
+  }
   return FD_OK;
 }
 
@@ -790,7 +683,28 @@ fd_status fd_tti_create(const fd_grid_desc* d, fd_tti* out) {
   if (!st) {
     e = dev_alloc(reinterpret_cast<void**>(&t->coef), 6 * t->ncell * 4);
     if (!e) e = t->scratch.ensure(64);
+    if (!e) e = t->err.ensure(16);
+    if (!e) e = cudaMemsetAsync(t->err.p, 0, 16, t->stream);
     if (e) st = cuda_fail(e, "model allocation");
+  }
+  t->spin_limit = default_spin_limit();
+  if (!st && t->R <= 4) {
+    // tensor maps of the TMA kernel: staged planes with the x halo rounded
+    // to four floats and R rows, per-point tiles, the six model fields
+    // stacked along z
+    const int W = tti::kQX + 8, H = tti::kQY + 2 * t->R;
+    for (int b = 0; b < 2 && !st; ++b) {
+      st = make_map(&t->halo_p[b], t->p[b], t->Nx, t->Ny, t->Nz, t->pitch, W, H);
+      if (!st) st = make_map(&t->halo_q[b], t->q[b], t->Nx, t->Ny, t->Nz, t->pitch, W, H);
+      if (!st)
+        st = make_map(&t->tile_p[b], t->p[b], t->Nx, t->Ny, t->Nz, t->pitch, tti::kQX, tti::kQY);
+      if (!st)
+        st = make_map(&t->tile_q[b], t->q[b], t->Nx, t->Ny, t->Nz, t->pitch, tti::kQX, tti::kQY);
+    }
+    if (!st)
+      st = make_map(&t->coef_map, t->coef, t->Nx, t->Ny, 6 * t->Nz, t->pitch, tti::kQX,
+                    tti::kQY);
+    t->maps = !st;
   }
   if (!st) {
     for (int b = 0; b < 2 && !e; ++b) {
@@ -820,7 +734,8 @@ fd_status fd_tti_destroy(fd_tti t) {
     if (t->q[b]) cudaFree(t->q[b]);
   }
   if (t->coef) cudaFree(t->coef);
-  for (DevBuf* b : {&t->inj, &t->rec, &t->stage_val, &t->stage_rec, &t->stage_in, &t->scratch})
+  for (DevBuf* b : {&t->inj, &t->rec, &t->stage_val, &t->stage_rec, &t->stage_in, &t->scratch,
+                    &t->err})
     b->release();
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);

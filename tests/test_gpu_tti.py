@@ -61,6 +61,18 @@ def test_forward_matches_the_oracle(fd, so):
     assert rel(q, ref["q"]) <= TOL, rel(q, ref["q"])
 
 
+@pytest.mark.parametrize("so", [4, 6, 8])
+def test_tall_grid_in_several_z_chunks_matches_the_oracle(fd, so):
+    """A grid tall enough that the launch cuts every tile column into several
+    z chunks (each with its own 2R-plane prologue), ragged in x and y."""
+    w = wl.tti_workload(n=(35, 21, 84), so=so, nbl=4, nt=40, seed=5)
+    rec, p, q = run_gpu(fd, w)
+    ref = otti.forward(ogrid(w), *model(w), w["nt"], w["src"], w["wavelet"], w["rec"])
+    assert rel(rec, ref["rec"]) <= TOL, rel(rec, ref["rec"])
+    assert rel(p, ref["p"]) <= TOL, rel(p, ref["p"])
+    assert rel(q, ref["q"]) <= TOL, rel(q, ref["q"])
+
+
 def test_single_step_from_random_state_elementwise(fd):
     w = wl.tti_workload(n=(41, 23, 35), so=8, nbl=6, nt=1)
     g0 = ogrid(w)
