@@ -654,19 +654,14 @@ def run_fwi(args):
 
 
 def tti_flops_per_point(R):
-    """Floating-point operations of one TTI point update as the kernels run it
-    (an FMA counts as two).  Per field, up to space order 8 (k_tti_q: each
-    plane's terms formed once when it enters, 32 x 8 tiles): the x
-    differences of the tile rows and the 2R halo rows, 3R (1 + R/4), and of
-    the thread's own row again, 3R; the y differences, 3R; the three R-term
-    second derivatives, 9R + 3; the three cross derivatives, 9R.  Wider
-    stencils form each cross term from R rows of R first differences:
-    18 R^2 + 18 R + 3 per field.  Then H_z of both fields, H_0 of p, the
+    """Floating-point operations of one TTI point update as the kernel runs it
+    (an FMA counts as two).  Per field (k_tti_q: each plane's terms formed
+    once when it enters, 32 x 8 tiles): the x differences of the tile rows
+    and the 2R halo rows, 3R (1 + R/4), and of the thread's own row again,
+    3R; the y differences, 3R; the three R-term second derivatives, 9R + 3;
+    the three cross derivatives, 9R.  Then H_z of both fields, H_0 of p, the
     coupling and the two damped leapfrog updates, 55 in all."""
-    if R <= 4:
-        per_field = 3 * R * (1 + R / 4) + 3 * R + 3 * R + 9 * R + 3 + 9 * R
-    else:
-        per_field = 18 * R * R + 18 * R + 3
+    per_field = 3 * R * (1 + R / 4) + 3 * R + 3 * R + 9 * R + 3 + 9 * R
     return int(round(2 * per_field + 55))
 
 
@@ -727,7 +722,7 @@ def run_tti(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_kind": "derived: 152 SMs x 128 FP32 "
                          "lanes x 2 x 2.07 GHz", "flops_per_point": tti_flops_per_point(R),
-                         "kernel": ("k_tti_q" if R <= 4 else "k_tti_step") +
+                         "kernel": "k_tti_q" +
                          " (avg over the timed step intervals)",
                          "avg_step_ms": step_ms},
             "clocks": clk, "gpu_launches": int(launches),

@@ -522,6 +522,17 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
     }
     size_t off = (static_cast<size_t>(zbeg) * a.Ny + gy) * a.pitch + gx;
     const size_t plane_stride = static_cast<size_t>(a.Ny) * a.pitch;
+    // adjoint mode: the imaging condition's e and gradient of the next plane
+    // are read one plane ahead, so their global-load latency overlaps the
+    // current plane (each point of the chunk is touched by this thread only);
+    // up to SO 8 (the wider stencils have no registers to spare and load them
+    // in the update)
+    constexpr bool kAdjAhead = MODE == kModeAdjoint && R <= 4;
+    float4 ein_nx = make_float4(0.f, 0.f, 0.f, 0.f), g_nx = ein_nx;
+    if (kAdjAhead && in_grid) {
+      ein_nx = __ldg(reinterpret_cast<const float4*>(a.e_in + off));
+      g_nx = *reinterpret_cast<const float4*>(a.grad + off);
+    }
 
     // ring slots: sk holds plane jk (split: halo plane ik, parity pk), sn
     // plane jn (parity pn; split: in the interior ring), sa tile ik
@@ -545,6 +556,13 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
 #define FD_Q(o) q[R + (o)]
         const int ik = k - zbeg;
         const int jk = ik + R;
+        float4 ein_c = ein_nx, g_c = g_nx;
+        if (kAdjAhead) {
+          if (in_grid && k + 1 < zend) {
+            ein_nx = __ldg(reinterpret_cast<const float4*>(a.e_in + off + plane_stride));
+            g_nx = *reinterpret_cast<const float4*>(a.grad + off + plane_stride);
+          }
+        }
         if constexpr (SPLIT) {
           bad |= !mbar_wait(bar_u0 + 8 * sk, pk, ov.spin_limit);
           bad |= !mbar_wait(bar_i0 + 8 * sn, pn, ov.spin_limit);
@@ -682,12 +700,13 @@ __device__ __forceinline__ void run_column(const CUtensorMap* tm_halo,
         }
         if (in_grid) {
           st_stream(out + off, res[0], res[1], res[2], res[3]);
-          if (MODE == kModeStoreE)
-            *reinterpret_cast<float4*>(a.e_out + off) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+          if (MODE == kModeStoreE)  // read back after the whole segment: not kept in L2
+            st_stream(a.e_out + off, ev[0], ev[1], ev[2], ev[3]);
           if (MODE == kModeAdjoint) {
-            const float4 ein = *reinterpret_cast<const float4*>(a.e_in + off);
+            const float4 ein =
+                kAdjAhead ? ein_c : __ldg(reinterpret_cast<const float4*>(a.e_in + off));
             const float4 uc = FD_Q(0);
-            float4 g = *reinterpret_cast<float4*>(a.grad + off);
+            float4 g = kAdjAhead ? g_c : *reinterpret_cast<const float4*>(a.grad + off);
             g.x -= uc.x * ein.x * a.inv_dt2;
             g.y -= uc.y * ein.y * a.inv_dt2;
             g.z -= uc.z * ein.z * a.inv_dt2;

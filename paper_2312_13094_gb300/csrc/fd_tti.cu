@@ -15,20 +15,15 @@
 // zero ghost, source scaling and trilinear points as in the isotropic path;
 // the source enters both fields, receivers interpolate p.
 //
-// Kernels (2.5D, one point per thread, a CTA owning a 32 x 8 xy tile and a
-// run of z planes).  Up to space order 8, k_tti_q (fd_tti_q.cuh): each plane
-// of p and q enters once, by TMA, with an R-wide halo; its in-plane second
-// derivatives and its first x and y differences are formed then, and every z
-// sum (D_zz, D_xz, D_yz) runs over per-thread register queues, so shared
-// memory holds only the entering plane, one plane of first x differences and
-// the update's per-point tiles.  The wider stencils (k_tti_step below), whose
-// queues would not fit in registers, keep the planes k-R .. k+R in a
-// shared-memory ring of 2R+1 slots per field, refilled with coalesced loads
-// (zero outside the grid: the read-only halo), and form the cross
-// derivatives as first differences of first differences from that ring, 4R^2
-// loads each.  The model enters through six per-cell fields (dt^2 v^2 / h^2,
-// 1 + 2 eps, sqrt(1 + 2 delta) and the axis n), computed once per model in
-// double precision.
+// Step kernel (2.5D, one point per thread, a CTA owning a 32 x 8 xy tile and
+// a run of z planes; k_tti_q, fd_tti_q.cuh): each plane of p and q enters
+// once, by TMA, with an R-wide halo; its in-plane second derivatives and its
+// first x and y differences are formed then, and every z sum (D_zz, D_xz,
+// D_yz) runs over per-thread register queues, so shared memory holds only
+// the entering plane, one plane of first x differences and the update's
+// per-point tiles.  The model enters through six per-cell fields
+// (dt^2 v^2 / h^2, 1 + 2 eps, sqrt(1 + 2 delta) and the axis n), computed
+// once per model in double precision.
 #include <math.h>
 #include <string.h>
 
@@ -65,9 +60,8 @@ struct fd_tti_s {
   double c[kMaxR + 1] = {}, d1[kMaxR + 1] = {};
   DevBuf inj, rec, stage_val, stage_rec, stage_in, scratch;
   DevBuf err;  // error word of the TMA kernel's bounded waits
-  // tensor maps of the TMA kernel (space orders up to 8), per buffer
+  // tensor maps of the step kernel, per buffer
   CUtensorMap halo_p[2], halo_q[2], tile_p[2], tile_q[2], coef_map;
-  bool maps = false;
   long long spin_limit = 0;
   int n_inj = 0, n_rec = 0;
   bool profiling = false;
@@ -77,23 +71,6 @@ struct fd_tti_s {
 };
 
 namespace {
-
-constexpr int kBX = 32, kBY = 8;
-
-struct TtiArgs {
-  const float* p;   // p^n, q^n
-  const float* q;
-  float* pn;        // p^{n-1} in, p^{n+1} out (in place)
-  float* qn;
-  const float* coef;
-  size_t ncell;
-  int Nx, Ny, Nz, pitch;
-  int nbl, nx, ny, nz;
-  int zchunk;
-  float bscale;
-  float c[kMaxR + 1];
-  float d[kMaxR + 1];
-};
 
 struct TtiInj {
   long long off;
@@ -112,125 +89,6 @@ __device__ __forceinline__ int depth(int g, int nbl, int n) {
   const int e = g - (n + nbl - 1);
   d = d > e ? d : e;
   return d > 0 ? d : 0;
-}
-
-// The six second derivatives of one field at the thread's point (units 1/h^2
-// folded into A): D_xx, D_yy, D_zz, D_xy, D_xz, D_yz.
-template <int R, int W, int PL, int S>
-__device__ __forceinline__ void derivatives(const float* ring, int s0, int c, const float* cw,
-                                            const float* dw, float out[6]) {
-  auto plane = [&](int o) -> const float* {
-    int s = s0 + o;
-    s = s >= S ? s - S : s;
-    s = s < 0 ? s + S : s;
-    return ring + s * PL;
-  };
-  const float* P0 = plane(0);
-  const float u0 = P0[c];
-  float xx = cw[0] * u0, yy = cw[0] * u0, zz = cw[0] * u0;
-  float xy = 0.f, xz = 0.f, yz = 0.f;
-#pragma unroll
-  for (int j = 1; j <= R; ++j) {
-    const float* Pp = plane(j);
-    const float* Pm = plane(-j);
-    xx = fmaf(cw[j], P0[c + j] + P0[c - j], xx);
-    yy = fmaf(cw[j], P0[c + j * W] + P0[c - j * W], yy);
-    zz = fmaf(cw[j], Pp[c] + Pm[c], zz);
-    // first differences along x of rows y+j, y-j and of planes k+j, k-j;
-    // along y of planes k+j, k-j
-    float axp = 0.f, axm = 0.f, azp = 0.f, azm = 0.f, ayp = 0.f, aym = 0.f;
-#pragma unroll
-    for (int i = 1; i <= R; ++i) {
-      axp = fmaf(dw[i], P0[c + j * W + i] - P0[c + j * W - i], axp);
-      axm = fmaf(dw[i], P0[c - j * W + i] - P0[c - j * W - i], axm);
-      azp = fmaf(dw[i], Pp[c + i] - Pp[c - i], azp);
-      azm = fmaf(dw[i], Pm[c + i] - Pm[c - i], azm);
-      ayp = fmaf(dw[i], Pp[c + i * W] - Pp[c - i * W], ayp);
-      aym = fmaf(dw[i], Pm[c + i * W] - Pm[c - i * W], aym);
-    }
-    xy = fmaf(dw[j], axp - axm, xy);
-    xz = fmaf(dw[j], azp - azm, xz);
-    yz = fmaf(dw[j], ayp - aym, yz);
-  }
-  out[0] = xx;
-  out[1] = yy;
-  out[2] = zz;
-  out[3] = xy;
-  out[4] = xz;
-  out[5] = yz;
-}
-
-template <int R>
-__global__ void __launch_bounds__(kBX* kBY) k_tti_step(const __grid_constant__ TtiArgs a) {
-  constexpr int W = kBX + 2 * R, H = kBY + 2 * R, PL = W * H, S = 2 * R + 1;
-  extern __shared__ float sm[];
-  float* sp = sm;
-  float* sq = sm + S * PL;
-  const int tid = threadIdx.x, tx = tid % kBX, ty = tid / kBX;
-  const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
-  const int z0 = blockIdx.z * a.zchunk;
-  const int z1 = min(z0 + a.zchunk, a.Nz);
-  const size_t plane = static_cast<size_t>(a.Ny) * a.pitch;
-  auto slot = [&](int z) {
-    const int s = z % S;
-    return s < 0 ? s + S : s;
-  };
-  auto load = [&](int z) {
-    float* dp = sp + slot(z) * PL;
-    float* dq = sq + slot(z) * PL;
-    const bool zin = z >= 0 && z < a.Nz;
-    for (int i = tid; i < PL; i += kBX * kBY) {
-      const int lx = i % W, ly = i / W, gx = x0 - R + lx, gy = y0 - R + ly;
-      float vp = 0.f, vq = 0.f;
-      if (zin && gx >= 0 && gx < a.Nx && gy >= 0 && gy < a.Ny) {
-        const size_t o = static_cast<size_t>(z) * plane + static_cast<size_t>(gy) * a.pitch + gx;
-        vp = a.p[o];
-        vq = a.q[o];
-      }
-      dp[i] = vp;
-      dq[i] = vq;
-    }
-  };
-  for (int z = z0 - R; z < z0 + R; ++z) load(z);
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool inside = gx < a.Nx && gy < a.Ny;
-  const int c = (ty + R) * W + tx + R;
-  const int dxy = depth(gx, a.nbl, a.nx) * depth(gx, a.nbl, a.nx) +
-                  depth(gy, a.nbl, a.ny) * depth(gy, a.nbl, a.ny);
-  for (int k = z0; k < z1; ++k) {
-    load(k + R);
-    __syncthreads();
-    if (inside) {
-      const int s0 = slot(k);
-      float dp[6], dq[6];
-      derivatives<R, W, PL, S>(sp, s0, c, a.c, a.d, dp);
-      derivatives<R, W, PL, S>(sq, s0, c, a.c, a.d, dq);
-      const size_t o = static_cast<size_t>(k) * plane + static_cast<size_t>(gy) * a.pitch + gx;
-      const float A = a.coef[o];
-      const float e2 = a.coef[a.ncell + o];
-      const float dl = a.coef[2 * a.ncell + o];
-      const float nx = a.coef[3 * a.ncell + o];
-      const float ny = a.coef[4 * a.ncell + o];
-      const float nz = a.coef[5 * a.ncell + o];
-      const float wxx = nx * nx, wyy = ny * ny, wzz = nz * nz;
-      const float wxy = 2.f * nx * ny, wxz = 2.f * nx * nz, wyz = 2.f * ny * nz;
-      const float lap_p = dp[0] + dp[1] + dp[2];
-      const float hz_p = wxx * dp[0] + wyy * dp[1] + wzz * dp[2] + wxy * dp[3] + wxz * dp[4] +
-                         wyz * dp[5];
-      const float hz_q = wxx * dq[0] + wyy * dq[1] + wzz * dq[2] + wxy * dq[3] + wxz * dq[4] +
-                         wyz * dq[5];
-      const float h0_p = lap_p - hz_p;
-      const float rp = e2 * h0_p + dl * hz_q;
-      const float rq = dl * h0_p + hz_q;
-      const int dz = depth(k, a.nbl, a.nz);
-      const float b = a.bscale * static_cast<float>(dxy + dz * dz);
-      const float pc = sp[s0 * PL + c], qc = sq[s0 * PL + c];
-      const float pm = a.pn[o], qm = a.qn[o];
-      a.pn[o] = (2.f * pc - (1.f - b) * pm + A * rp) / (1.f + b);
-      a.qn[o] = (2.f * qc - (1.f - b) * qm + A * rq) / (1.f + b);
-    }
-    __syncthreads();
-  }
 }
 
 // Model fields on the padded, pitched grid (edge replication into the layer),
@@ -318,27 +176,6 @@ __global__ void k_tti_inject(const TtiInj* __restrict__ inj, int n, const float*
 }
 
 template <int R>
-constexpr size_t tti_smem() {
-  return 2u * (2 * R + 1) * (kBX + 2 * R) * (kBY + 2 * R) * sizeof(float);
-}
-
-template <int R>
-cudaError_t launch_r(const TtiArgs& a, dim3 grid, cudaStream_t s) {
-  static unsigned long long done = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (!(done & (1ull << (dev & 63)))) {
-    cudaError_t e = cudaFuncSetAttribute(k_tti_step<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(tti_smem<R>()));
-    if (e) return e;
-    done |= 1ull << (dev & 63);
-  }
-  k_tti_step<R><<<grid, kBX * kBY, tti_smem<R>(), s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int R>
 cudaError_t launch_q(const tti::QMaps& M, const tti::QArgs& qa, dim3 grid, cudaStream_t s) {
   static unsigned long long done = 0;
   int dev = 0;
@@ -362,17 +199,10 @@ cudaError_t launch_q_r(int R, const tti::QMaps& M, const tti::QArgs& qa, dim3 gr
     case 2: return launch_q<2>(M, qa, grid, s);
     case 3: return launch_q<3>(M, qa, grid, s);
     case 4: return launch_q<4>(M, qa, grid, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_step(int R, const TtiArgs& a, dim3 grid, cudaStream_t s) {
-  count_launch();
-  switch (R) {  // space orders up to 8 run k_tti_q (launch_q_r)
-    case 5: return launch_r<5>(a, grid, s);
-    case 6: return launch_r<6>(a, grid, s);
-    case 7: return launch_r<7>(a, grid, s);
-    case 8: return launch_r<8>(a, grid, s);
+    case 5: return launch_q<5>(M, qa, grid, s);
+    case 6: return launch_q<6>(M, qa, grid, s);
+    case 7: return launch_q<7>(M, qa, grid, s);
+    case 8: return launch_q<8>(M, qa, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -515,60 +345,38 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
       drec = static_cast<float*>(t->stage_rec.p);
     }
   }
-  TtiArgs a;
-  memset(&a, 0, sizeof(a));
-  a.coef = t->coef;
-  a.ncell = t->ncell;
-  a.Nx = t->Nx;
-  a.Ny = t->Ny;
-  a.Nz = t->Nz;
-  a.pitch = t->pitch;
-  a.nbl = t->d.nbl;
-  a.nx = t->d.nx;
-  a.ny = t->d.ny;
-  a.nz = t->d.nz;
-  a.zchunk = std::max(4 * t->R, 64);
-  a.bscale = t->bscale;
-  for (int j = 0; j <= kMaxR; ++j) {
-    a.c[j] = j <= t->R ? float(t->c[j]) : 0.f;
-    a.d[j] = j <= t->R ? float(t->d1[j]) : 0.f;
-  }
-  const dim3 grid((t->Nx + kBX - 1) / kBX, (t->Ny + kBY - 1) / kBY,
-                  (t->Nz + a.zchunk - 1) / a.zchunk);
-  // space orders up to 8: the TMA kernel with register queues; its z chunks
-  // are cut so that the launch fills at least four waves of two CTAs per SM
-  const bool qk = t->maps;
+  // the step kernel's arguments; its z chunks are cut so that the launch
+  // fills at least four waves of the resident CTAs
   tti::QArgs qa;
   memset(&qa, 0, sizeof(qa));
-  dim3 qgrid(1, 1, 1);
-  if (qk) {
-    qa.err = static_cast<int*>(t->err.p);
-    qa.Nx = t->Nx;
-    qa.Ny = t->Ny;
-    qa.Nz = t->Nz;
-    qa.pitch = t->pitch;
-    qa.nbl = t->d.nbl;
-    qa.nx = t->d.nx;
-    qa.ny = t->d.ny;
-    qa.nz = t->d.nz;
-    qa.spin_limit = t->spin_limit;
-    qa.bscale = t->bscale;
-    for (int j = 0; j <= kMaxR; ++j) {
-      qa.c[j] = a.c[j];
-      qa.d[j] = a.d[j];
-    }
+  qa.err = static_cast<int*>(t->err.p);
+  qa.Nx = t->Nx;
+  qa.Ny = t->Ny;
+  qa.Nz = t->Nz;
+  qa.pitch = t->pitch;
+  qa.nbl = t->d.nbl;
+  qa.nx = t->d.nx;
+  qa.ny = t->d.ny;
+  qa.nz = t->d.nz;
+  qa.spin_limit = t->spin_limit;
+  qa.bscale = t->bscale;
+  for (int j = 0; j <= kMaxR; ++j) {
+    qa.c[j] = j <= t->R ? float(t->c[j]) : 0.f;
+    qa.d[j] = j <= t->R ? float(t->d1[j]) : 0.f;
+  }
+  {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long cols = (long long)((t->Nx + tti::kQX - 1) / tti::kQX) *
                            ((t->Ny + tti::kQY - 1) / tti::kQY);
-    const long long want = 4LL * 2 * std::max(sms, 1);
+    const long long want = 4LL * (t->R <= 4 ? 2 : 1) * std::max(sms, 1);
     int chunks = int(std::max<long long>(1, (want + cols - 1) / cols));
     chunks = std::min(chunks, std::max(1, t->Nz / (8 * t->R)));
     qa.zchunk = (t->Nz + chunks - 1) / chunks;
-    qgrid = dim3((t->Nx + tti::kQX - 1) / tti::kQX, (t->Ny + tti::kQY - 1) / tti::kQY,
-                 (t->Nz + qa.zchunk - 1) / qa.zchunk);
   }
+  const dim3 qgrid((t->Nx + tti::kQX - 1) / tti::kQX, (t->Ny + tti::kQY - 1) / tti::kQY,
+                   (t->Nz + qa.zchunk - 1) / qa.zchunk);
   if (t->profiling) cudaEventRecord(t->ev0, t->stream);
   for (int s = 0; s < nsteps; ++s) {
     const int cur = t->cur;
@@ -577,24 +385,15 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
           t->p[cur], static_cast<const TtiRec*>(t->rec.p), nrec, drec + size_t(s) * nrec);
       count_launch();
     }
-    a.p = t->p[cur];
-    a.q = t->q[cur];
-    a.pn = t->p[cur ^ 1];
-    a.qn = t->q[cur ^ 1];
-    if (qk) {
-      tti::QMaps M;
-      M.halo_p = t->halo_p[cur];
-      M.halo_q = t->halo_q[cur];
-      M.prev_p = t->tile_p[cur ^ 1];
-      M.prev_q = t->tile_q[cur ^ 1];
-      M.coef = t->coef_map;
-      qa.pn = a.pn;
-      qa.qn = a.qn;
-      e = launch_q_r(t->R, M, qa, qgrid, t->stream);
-    } else {
-      e = launch_step(t->R, a, grid, t->stream);
-    }
-    if (e) return cuda_fail(e, "TTI step launch");
+    tti::QMaps M;
+    M.halo_p = t->halo_p[cur];
+    M.halo_q = t->halo_q[cur];
+    M.prev_p = t->tile_p[cur ^ 1];
+    M.prev_q = t->tile_q[cur ^ 1];
+    M.coef = t->coef_map;
+    qa.pn = t->p[cur ^ 1];
+    qa.qn = t->q[cur ^ 1];
+    if ((e = launch_q_r(t->R, M, qa, qgrid, t->stream))) return cuda_fail(e, "TTI step launch");
     if (t->n_inj) {
       k_tti_inject<<<(t->n_inj + 127) / 128, 128, 0, t->stream>>>(
           static_cast<const TtiInj*>(t->inj.p), t->n_inj, dval + size_t(n0 + s) * nsrc, t->coef,
@@ -626,7 +425,7 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
   }
   e = cudaStreamSynchronize(t->stream);
   if (e) return cuda_fail(e, "stream synchronize");
-  if (qk && nsteps > 0) {
+  if (nsteps > 0) {
     int flag = 0;
     e = cudaMemcpy(&flag, t->err.p, sizeof(flag), cudaMemcpyDeviceToHost);
     if (e) return cuda_fail(e, "error word");
@@ -688,11 +487,11 @@ fd_status fd_tti_create(const fd_grid_desc* d, fd_tti* out) {
     if (e) st = cuda_fail(e, "model allocation");
   }
   t->spin_limit = default_spin_limit();
-  if (!st && t->R <= 4) {
+  if (!st) {
     // tensor maps of the TMA kernel: staged planes with the x halo rounded
-    // to four floats and R rows, per-point tiles, the six model fields
+    // up to four floats and R rows, per-point tiles, the six model fields
     // stacked along z
-    const int W = tti::kQX + 8, H = tti::kQY + 2 * t->R;
+    const int W = tti::kQX + 2 * ((t->R + 3) / 4 * 4), H = tti::kQY + 2 * t->R;
     for (int b = 0; b < 2 && !st; ++b) {
       st = make_map(&t->halo_p[b], t->p[b], t->Nx, t->Ny, t->Nz, t->pitch, W, H);
       if (!st) st = make_map(&t->halo_q[b], t->q[b], t->Nx, t->Ny, t->Nz, t->pitch, W, H);
@@ -704,7 +503,6 @@ fd_status fd_tti_create(const fd_grid_desc* d, fd_tti* out) {
     if (!st)
       st = make_map(&t->coef_map, t->coef, t->Nx, t->Ny, 6 * t->Nz, t->pitch, tti::kQX,
                     tti::kQY);
-    t->maps = !st;
   }
   if (!st) {
     for (int b = 0; b < 2 && !e; ++b) {
@@ -886,8 +684,8 @@ fd_status fd_tti_get_info(fd_tti t, fd_grid_info* info) {
   info->ny_pad = t->Ny;
   info->nz_pad = t->Nz;
   info->pitch = t->pitch;
-  info->tile_x = kBX;
-  info->tile_y = kBY;
+  info->tile_x = tti::kQX;
+  info->tile_y = tti::kQY;
   info->v_max = t->vmax;
   info->cfl_limit = t->cfl;
   info->launches = fd_launch_count();

@@ -1,6 +1,7 @@
-// TTI step for space orders 2..8 with register queues and TMA staging
-// (included by fd_tti.cu; same equations as k_tti_step, Sec. IV-B and App. A,
-// Eq. rot).
+// TTI step with register queues and TMA staging (included by fd_tti.cu;
+// Sec. IV-B and App. A, Eq. rot).  Space orders up to 8 run two 256-thread
+// CTAs per SM; the wider stencils, whose queues take about 200 registers,
+// one.
 //
 // One point per thread on a 32 x 8 tile, a CTA streaming a run of z planes.
 // Every derivative is split by what it needs:
@@ -30,12 +31,15 @@ constexpr int kQPF = 2;                             // planes in flight ahead
 
 template <int R>
 struct QGeom {
-  static constexpr int RX = 4;  // x halo of the staged tile: 16-byte aligned TMA x coordinate
+  // x halo of the staged tile: R rounded up to 4 floats (16-byte aligned TMA x coordinate)
+  static constexpr int RX = ((R + 3) / 4) * 4;
   static constexpr int W = kQX + 2 * RX, H = kQY + 2 * R;
   static constexpr uint32_t UBYTES = W * H * 4;
   static constexpr uint32_t UP = (UBYTES + 127) / 128 * 128;  // one field's staged plane
   static constexpr int SU = kQPF + 1, SA = kQPF + 1;
   static constexpr int EH = kQY + 2 * R;  // rows of the dx scratch
+  static constexpr int NE = (EH + kQY - 1) / kQY;  // scratch rows per thread
+  static constexpr int CTAS = R <= 4 ? 2 : 1;       // resident CTAs per SM
   static constexpr uint32_t XP = (kQX * EH * 4 + 127) / 128 * 128;
   static constexpr uint32_t TBYTES = kQX * kQY * 4;  // one per-point tile
   static constexpr uint32_t OFF_X = 2 * SU * UP;      // dx scratch: [field][buffer]
@@ -78,7 +82,7 @@ __device__ __forceinline__ void qpush(float (&q)[N], float v) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kQT, 2)
+__global__ void __launch_bounds__(kQT, QGeom<R>::CTAS)
     k_tti_q(const __grid_constant__ QMaps M, const __grid_constant__ QArgs a) {
   using G = QGeom<R>;
   extern __shared__ unsigned char qsm_raw[];
@@ -152,11 +156,9 @@ __global__ void __launch_bounds__(kQT, 2)
   const bool inside = gx < a.Nx && gy < a.Ny;
   const int dxy = qdepth(gx, a.nbl, a.nx) * qdepth(gx, a.nbl, a.nx) +
                   qdepth(gy, a.nbl, a.ny) * qdepth(gy, a.nbl, a.ny);
-  // byte offsets: own point in a staged plane, and the two scratch rows this
-  // thread fills (scratch row e = staged row e, tile row e - R)
+  // byte offsets: own point in a staged plane; the scratch rows this thread
+  // fills are e = ty + 8m (scratch row e = staged row e, tile row e - R)
   const uint32_t cown = 4u * ((ty + R) * G::W + tx + G::RX);
-  const uint32_t crow2 = 4u * ((ty + kQY) * G::W + tx + G::RX);
-  const bool two = ty + kQY < G::EH;
   const uint32_t cx = 4u * ((ty + R) * kQX + tx);
   const size_t plane = static_cast<size_t>(a.Ny) * a.pitch;
   size_t off = static_cast<size_t>(z0) * plane + static_cast<size_t>(gy) * a.pitch + gx;
@@ -188,22 +190,20 @@ __global__ void __launch_bounds__(kQT, 2)
         dx = fmaf(a.d[j], xp - xm, dx);
         dy = fmaf(a.d[j], yp - ym, dy);
       }
-      // first x differences of scratch rows ty and ty + 8 (staged rows)
+      // first x differences of the scratch rows ty + 8m (staged rows)
       const uint32_t X = sbase + G::OFF_X + (2 * f + buf) * G::XP;
-      {
-        const uint32_t r1 = 4u * (ty * G::W + tx + G::RX);
-        float e1 = 0.f;
 #pragma unroll
-        for (int j = 1; j <= R; ++j) e1 = fmaf(a.d[j], lds1(P + r1 + 4 * j) - lds1(P + r1 - 4 * j), e1);
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(X + 4u * (ty * kQX + tx)), "f"(e1) : "memory");
-      }
-      if (two) {
-        float e2 = 0.f;
+      for (int m = 0; m < G::NE; ++m) {
+        const int e = ty + m * kQY;
+        if (m == 0 || e < G::EH) {
+          const uint32_t re = 4u * (e * G::W + tx + G::RX);
+          float ex = 0.f;
 #pragma unroll
-        for (int j = 1; j <= R; ++j)
-          e2 = fmaf(a.d[j], lds1(P + crow2 + 4 * j) - lds1(P + crow2 - 4 * j), e2);
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(X + 4u * ((ty + kQY) * kQX + tx)), "f"(e2)
-                     : "memory");
+          for (int j = 1; j <= R; ++j)
+            ex = fmaf(a.d[j], lds1(P + re + 4 * j) - lds1(P + re - 4 * j), ex);
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(X + 4u * (e * kQX + tx)), "f"(ex)
+                       : "memory");
+        }
       }
       uo[f] = u0;
       xxo[f] = xx;

@@ -105,7 +105,9 @@ def test_adjoint_schedules_and_tiles_agree_bitwise(fd):
                         (fd.FD_SCHED_WAVES, None)):
         grad, loss = grad_with(sched, tile)
         np.testing.assert_array_equal(grad, ref[0])
-        assert loss == ref[1]
+        # the misfit is a double sum accumulated with atomics: equal up to the
+        # order of the additions
+        assert abs(loss - ref[1]) <= 1e-12 * abs(ref[1])
 
 
 def test_tuned_adjoint_equals_equal_shares(fd):
