@@ -296,18 +296,29 @@ __device__ __forceinline__ void update4_layer(const float lap[4], const float sr
                                               const float4& Av, const float dxx[4], float dzz,
                                               float bscale, const bool ok[4], float res[4],
                                               float ev[4]) {
+  // lanes (0,1) and (2,3) as packed pairs, each operation rounding every lane
+  // exactly as its scalar form; the division stays per lane
+  const float2 one = make_float2(1.0f, 1.0f), two = make_float2(2.0f, 2.0f);
+  const float2 bs2 = make_float2(bscale, bscale), dz2 = make_float2(dzz, dzz);
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const float b = bscale * (dxx[l] + dzz);
-    const float uc = lane(uc4, l);
-    const float ls = __fadd_rn(lap[l], src[l]);
-    const float e = __fmul_rn(lane(Av, l), ls);
-    float t = fmaf(lane(Av, l), ls, fmaf(-(1.0f - b), lane(up, l), 2.0f * uc));
+  for (int p = 0; p < 2; ++p) {
+    const float2 b = __fmul2_rn(bs2, __fadd2_rn(make_float2(dxx[2 * p], dxx[2 * p + 1]), dz2));
+    const float2 ls = __fadd2_rn(make_float2(lap[2 * p], lap[2 * p + 1]),
+                                 make_float2(src[2 * p], src[2 * p + 1]));
+    const float2 a2 = half2of(Av, p);
+    const float2 e = __fmul2_rn(a2, ls);
+    const float2 omb = __fadd2_rn(one, make_float2(-b.x, -b.y));  // 1 - b
+    const float2 t2 = __ffma2_rn(a2, ls,
+                                 __ffma2_rn(make_float2(-omb.x, -omb.y), half2of(up, p),
+                                            __fmul2_rn(two, half2of(uc4, p))));
+    const float2 d = __fadd2_rn(one, b);
     // inside the layer divide by 1+b (fast reciprocal; select, no branch)
-    const float td = __fdividef(t, 1.0f + b);
-    t = (b != 0.0f) ? td : t;
-    res[l] = ok[l] ? t : 0.0f;
-    ev[l] = ok[l] ? e : 0.0f;
+    const float tx = (b.x != 0.0f) ? __fdividef(t2.x, d.x) : t2.x;
+    const float ty = (b.y != 0.0f) ? __fdividef(t2.y, d.y) : t2.y;
+    res[2 * p] = ok[2 * p] ? tx : 0.0f;
+    res[2 * p + 1] = ok[2 * p + 1] ? ty : 0.0f;
+    ev[2 * p] = ok[2 * p] ? e.x : 0.0f;
+    ev[2 * p + 1] = ok[2 * p + 1] ? e.y : 0.0f;
   }
 }
 
