@@ -115,7 +115,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, watts, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -126,11 +126,16 @@ class ClockSampler:
                 smax.append(float(parts[1]))
             except ValueError:
                 continue
+            try:
+                watts.append(float(parts[2]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[3:7]):
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
+                "power_w": statistics.median(watts) if watts else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -333,6 +338,8 @@ def run_ours(args, w, world, rank, local):
                 dist.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            eclk = ClockSampler(local)
+            eclk.start()
             e0.record(stream)
             for _ in range(args.steps):
                 g.set_model(v_host)
@@ -343,7 +350,7 @@ def run_ours(args, w, world, rank, local):
             e2e_ms = e0.elapsed_time(e1)
             e2e = {"ms": e2e_ms,
                    "h2d": v_host.numel() * 4 + wav_host.numel() * 4,
-                   "d2h": rec_host.numel() * 4}
+                   "d2h": rec_host.numel() * 4, "clocks": eclk.stop()}
         g.close()
 
     t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device="cuda", dtype=torch.float64)
@@ -389,7 +396,8 @@ def run_ours(args, w, world, rank, local):
     if e2e:
         line["e2e"] = {"value": world * npts * nt * args.steps / (e2e_max * 1e-3) / 1e9,
                        "unit": "Gpts/s", "h2d_bytes_per_step": e2e["h2d"],
-                       "d2h_bytes_per_step": e2e["d2h"]}
+                       "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e_max / args.steps,
+                       "clocks": e2e["clocks"]}
     if not args.no_cpu_baseline and world == 1:
         r, k, cores, el = cpu_oracle_rate(w, seconds=args.ref_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
