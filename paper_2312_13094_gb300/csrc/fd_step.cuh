@@ -799,7 +799,7 @@ fail:
       if (ov.debug_skip_plane >= 0 && z_u0 + j == ov.debug_skip_plane) continue;
       mbar_wait(bar_u0 + 8 * (j % C::SU), (j / C::SU) & 1, ov.spin_limit);
     }
-    if (SPLIT) {
+    if constexpr (SPLIT) {
       for (int j = max(0, ji_next - C::SI); j < ji_next; ++j) {
         if (ov.debug_skip_plane >= 0 && zbeg - R + j == ov.debug_skip_plane) continue;
         mbar_wait(bar_i0 + 8 * (j % C::SI), (j / C::SI) & 1, ov.spin_limit);

@@ -427,7 +427,8 @@ fd_status propagate(fd_tti t, int n0, int nsteps, const fd_points* src, const fl
   if (e) return cuda_fail(e, "stream synchronize");
   if (nsteps > 0) {
     int flag = 0;
-    e = cudaMemcpy(&flag, t->err.p, sizeof(flag), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(&flag, t->err.p, sizeof(flag), cudaMemcpyDeviceToHost, t->stream);
+    if (!e) e = cudaStreamSynchronize(t->stream);
     if (e) return cuda_fail(e, "error word");
     if (flag) {
       cudaMemsetAsync(t->err.p, 0, sizeof(int), t->stream);
