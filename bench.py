@@ -665,11 +665,11 @@ def tti_flops_per_point(R):
     """Floating-point operations of one TTI point update as the kernel runs it
     (an FMA counts as two).  Per field (k_tti_q: each plane's terms formed
     once when it enters, 32 x 8 tiles): the x differences of the tile rows
-    and the 2R halo rows, 3R (1 + R/4), and of the thread's own row again,
-    3R; the y differences, 3R; the three R-term second derivatives, 9R + 3;
-    the three cross derivatives, 9R.  Then H_z of both fields, H_0 of p, the
-    coupling and the two damped leapfrog updates, 55 in all."""
-    per_field = 3 * R * (1 + R / 4) + 3 * R + 3 * R + 9 * R + 3 + 9 * R
+    and the 2R halo rows, 3R (1 + R/4); the y differences, 3R; the three
+    R-term second derivatives, 9R + 3; the three cross derivatives, 9R.  Then
+    H_z of both fields, H_0 of p, the coupling and the two damped leapfrog
+    updates, 55 in all."""
+    per_field = 3 * R * (1 + R / 4) + 3 * R + 9 * R + 3 + 9 * R
     return int(round(2 * per_field + 55))
 
 

@@ -175,19 +175,18 @@ __global__ void __launch_bounds__(kQT, QGeom<R>::CTAS)
   auto enter = [&](int i) -> bool {
     bad |= !mbar_wait(bar_u0 + 8 * su, pu, a.spin_limit);
     const int buf = i & 1;
-    float dxo[2], dyo[2], xxo[2], yyo[2], uo[2];
+    float dyo[2], xxo[2], yyo[2], uo[2];
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       const uint32_t P = sbase + (2 * su + f) * G::UP;
       const float u0 = lds1(P + cown);
-      float xx = a.c[0] * u0, yy = a.c[0] * u0, dx = 0.f, dy = 0.f;
+      float xx = a.c[0] * u0, yy = a.c[0] * u0, dy = 0.f;
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const float xp = lds1(P + cown + 4 * j), xm = lds1(P + cown - 4 * j);
         const float yp = lds1(P + cown + 4 * j * G::W), ym = lds1(P + cown - 4 * j * G::W);
         xx = fmaf(a.c[j], xp + xm, xx);
         yy = fmaf(a.c[j], yp + ym, yy);
-        dx = fmaf(a.d[j], xp - xm, dx);
         dy = fmaf(a.d[j], yp - ym, dy);
       }
       // first x differences of the scratch rows ty + 8m (staged rows)
@@ -208,7 +207,6 @@ __global__ void __launch_bounds__(kQT, QGeom<R>::CTAS)
       uo[f] = u0;
       xxo[f] = xx;
       yyo[f] = yy;
-      dxo[f] = dx;
       dyo[f] = dy;
     }
     if (__syncthreads_or(bad)) return false;
@@ -223,8 +221,10 @@ __global__ void __launch_bounds__(kQT, QGeom<R>::CTAS)
 #pragma unroll
       for (int j = 1; j <= R; ++j)
         xy = fmaf(a.d[j], lds1(X + cx + 4 * j * kQX) - lds1(X + cx - 4 * j * kQX), xy);
+      // the own row's first x difference is scratch row ty + R, written before
+      // the barrier (the same sum in the same order)
       qpush(qu[f], uo[f]);
-      qpush(qdx[f], dxo[f]);
+      qpush(qdx[f], lds1(X + cx));
       qpush(qdy[f], dyo[f]);
       qpush(qxx[f], xxo[f]);
       qpush(qyy[f], yyo[f]);
