@@ -21,9 +21,11 @@
 // floats so that every tile's TMA x coordinate stays 16-byte aligned.  Ghost
 // layers beyond the grid are zero and never written.
 //
-// Step.  One launch of the plain sweep kernel steps every box (the boxes are
+// Step.  One launch of the plain step kernel steps every box (the boxes are
 // the "shots" of the launch, with their own tensor maps, tables and array
-// offsets that keep the damping layer in global coordinates).  A pack kernel
+// offsets that keep the damping layer in global coordinates), on column
+// waves over the boxes one after another unless the grid asks for equal
+// shares or a CTA count.  A pack kernel
 // then copies the R updated layers next to each face with a neighbour into
 // that face's contiguous message, and an unpack kernel copies every message
 // block into the receiving box's ghost layers: the whole message for a face
